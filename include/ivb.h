@@ -1,0 +1,226 @@
+/*
+ * ivb.h -- C ABI of the GB300 (sm_103a) interval Mean Value Form subdomain
+ * bounding library.
+ *
+ * Method (Zhang et al., "Accelerating Deterministic Global Optimization via
+ * GPU-parallel Interval Arithmetic"): each branch-and-bound node's box is
+ * temporarily split into a uniform grid of subdomains (Section 2.2, splitting
+ * technique; Section 3.1 Step 1); on every subdomain the objective and the
+ * constraints are enclosed with the interval Mean Value Form
+ * f(c) + <grad F(X), X - c> (Definition 5; Section 3.1 Step 2) in outward
+ * rounded binary64; the enclosures are reduced to each node's refinement
+ * (Section 3.1 Step 3): lower bound of the objective and an infeasibility
+ * flag (Section 3.1, pruning by the feasibility check).
+ *
+ * Conventions for every entry point:
+ *  - Pointers are plain host or device pointers; the library asks CUDA which
+ *    kind each one is. The caller owns every array it passes in.
+ *  - Calls are ordered on `cuda_stream` (NULL = the legacy default stream).
+ *    A call that reads or writes any host array returns after the work is
+ *    complete; a call on device arrays only returns after enqueueing.
+ *  - Errors are reported by the return code, never by aborting; the text of
+ *    the last error of a handle is available through ivb_last_error().
+ *  - A handle is not re-entrant: use one handle per host thread.
+ */
+#ifndef IVB_H
+#define IVB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IVB_ABI_VERSION 1
+#define IVB_MAX_VARS 32        /* variables per problem */
+#define IVB_MAX_OUTPUTS 64     /* objective + constraints per problem */
+#define IVB_MAX_OPS 1048576    /* tape entries per problem */
+
+typedef enum {
+    IVB_OK = 0,
+    IVB_EINVAL = 1,    /* an argument failed validation (message says which) */
+    IVB_ENOMEM = 2,    /* device or pinned host allocation failed */
+    IVB_ECUDA = 3,     /* a CUDA runtime call failed (message has its text) */
+    IVB_ETAPE = 4,     /* the tape is malformed */
+    IVB_ETIMEOUT = 5,  /* a bounded device wait ran out */
+    IVB_ENOTSUP = 6    /* option combination not supported */
+} ivb_status;
+
+/* Tape alphabet: the intrinsic functions of a factorable function
+ * (Definition 4), one DAG for objective and constraints (Section 3.2, Fig. 5). */
+enum {
+    IVB_OP_VAR = 0,    /* x_a                         (a = variable index)  */
+    IVB_OP_CONST = 1,  /* the constant c                                    */
+    IVB_OP_ADD = 2,    /* v_a + v_b                                         */
+    IVB_OP_SUB = 3,    /* v_a - v_b                                         */
+    IVB_OP_MUL = 4,    /* v_a * v_b                                         */
+    IVB_OP_DIV = 5,    /* v_a / v_b                                         */
+    IVB_OP_SQR = 6,    /* v_a^2                                             */
+    IVB_OP_SQRT = 7,   /* sqrt(v_a)                                         */
+    IVB_OP_EXP = 8,    /* exp(v_a)                                          */
+    IVB_OP_LOG = 9,    /* log(v_a)                                          */
+    IVB_OP_NEG = 10    /* -v_a                                              */
+};
+
+/* output kinds of the NLP in Section 3.1: min f s.t. g_i <= 0, h_j = 0 */
+enum { IVB_OUT_OBJ = 0, IVB_OUT_INEQ = 1, IVB_OUT_EQ = 2 };
+
+/* one tape entry, 24 bytes: operands a, b index EARLIER entries */
+typedef struct {
+    uint8_t op;
+    uint8_t _pad[3];
+    int32_t a, b;
+    double c;
+} ivb_op;
+
+typedef struct {
+    int32_t n_vars;            /* 1 .. IVB_MAX_VARS                         */
+    int32_t n_ops;             /* 1 .. IVB_MAX_OPS                          */
+    int32_t n_outputs;         /* 1 .. IVB_MAX_OUTPUTS                      */
+    const ivb_op* ops;         /* host array [n_ops]                        */
+    const int32_t* out_idx;    /* host array [n_outputs]: tape entry        */
+    const uint8_t* out_kind;   /* host array [n_outputs]: IVB_OUT_*; exactly
+                                  one IVB_OUT_OBJ                           */
+} ivb_tape;
+
+enum { IVB_GRAD_FORWARD = 0, IVB_GRAD_ADJOINT = 1 };
+enum { IVB_FORM_MVF = 0, IVB_FORM_NIE = 1, IVB_FORM_MVF_NIE = 2 };
+enum { IVB_SPLIT_UNIFORM = 0, IVB_SPLIT_LARGEST = 1, IVB_SPLIT_ADAPTIVE = 2 };
+
+typedef struct {
+    int32_t grad_mode;         /* IVB_GRAD_ADJOINT (default) or _FORWARD       */
+    int32_t form;              /* IVB_FORM_MVF (default), _NIE, _MVF_NIE       */
+    int32_t filter;            /* 1: objective minimum skips subdomains whose
+                                  constraints are certainly violated (0)      */
+    int32_t batched;           /* 1 (default): all nodes of a call in one
+                                  persistent launch from a device node queue;
+                                  0: one launch per node (plain path)         */
+    int32_t use_graph;         /* 1 (default): replay the batched call as a
+                                  CUDA graph                                  */
+    int32_t autotune;          /* 1 (default): pick block size, blocks per SM
+                                  and tile on first use                       */
+    int32_t block_threads;     /* threads per block; 0 = tuned / default     */
+    int32_t blocks_per_sm;     /* resident blocks per SM; 0 = tuned/default  */
+    int32_t tile;              /* subdomains a block grabs at a time; 0 = auto */
+    int32_t max_nodes;         /* capacity of one call (default 4096)       */
+    int32_t frame_in_shared;   /* -1 auto (default), 0 global, 1 shared     */
+} ivb_options;
+
+typedef struct ivb_problem ivb_problem;
+
+/* Fill `opt` with the defaults listed above. */
+void ivb_options_default(ivb_options* opt);
+
+/* Validate the tape, compile it into the device program and upload it.
+ * Rejects (IVB_ETAPE): unknown opcodes, operands that do not refer to an
+ * earlier entry, VAR indices outside [0, n_vars), non-finite constants,
+ * outputs that are out of range, and anything other than exactly one
+ * objective. `opt` may be NULL (defaults). On success *out owns device
+ * memory until ivb_destroy(). */
+ivb_status ivb_create_problem(const ivb_tape* tape, const ivb_options* opt, ivb_problem** out);
+
+/* Steps 1-3 of Subdomain Lower Bounding (Section 3.1) for a batch of nodes.
+ *   boxes          [n_nodes][n_vars][2] node boxes (lo, hi), finite, lo <= hi,
+ *                  |endpoint| <= 2^1000
+ *   splits_per_dim [n_nodes][n_vars], each >= 1, product <= 2^31 per node;
+ *                  subdomain k of a node has j_i = (k / prod_{l<i} N_l) mod N_i
+ *                  (dimension 0 fastest, as in Section 3.1.1)
+ *   out_lb         [n_nodes] min over subdomains of lo(F_obj) (may be -inf)
+ *   out_infeasible [n_nodes] 1 if some inequality's refinement lower end is
+ *                  > 0 or some equality's refinement excludes 0
+ * Host and device pointers may be mixed. 0 <= n_nodes <= max_nodes; an
+ * empty batch returns IVB_OK without touching any array. */
+ivb_status ivb_bound_nodes(ivb_problem* p, int32_t n_nodes, const double* boxes,
+                           const int32_t* splits_per_dim, double* out_lb,
+                           uint8_t* out_infeasible, void* cuda_stream);
+
+/* As ivb_bound_nodes, with optional extra results (NULL to skip):
+ *   out_ub     [n_nodes] smallest hi(f(c_k)) over subdomains whose centre
+ *              c_k is certified feasible (every inequality has hi(g(c_k)) <= 0;
+ *              none when equalities exist); +inf if none: a rigorous upper
+ *              bound on the node's constrained minimum
+ *   out_minlo  [n_nodes][n_outputs] refinement lower ends of every output
+ *   out_maxhi  [n_nodes][n_outputs] refinement upper ends of every output */
+ivb_status ivb_bound_nodes_ex(ivb_problem* p, int32_t n_nodes, const double* boxes,
+                              const int32_t* splits_per_dim, double* out_lb,
+                              uint8_t* out_infeasible, double* out_ub, double* out_minlo,
+                              double* out_maxhi, void* cuda_stream);
+
+/* Per-subdomain enclosures (Step 2 without the reduction) for subdomains
+ * first .. first+count-1 of ONE node:
+ *   out_F  [count][n_outputs][2]          the enclosure of the chosen form
+ *   out_Fc [count][n_outputs][2]          rigorous point value f(c_k) (or NULL)
+ *   out_G  [count][n_outputs][n_vars][2]  gradient enclosure on X_k (or NULL)
+ * count <= 2^24 per call. */
+ivb_status ivb_enclose(ivb_problem* p, const double* box, const int32_t* splits_per_dim,
+                       int64_t first, int64_t count, double* out_F, double* out_Fc,
+                       double* out_G, void* cuda_stream);
+
+/* Round-to-nearest point values and reverse-mode gradients of every output:
+ *   x [n_points][n_vars] -> out_f [n_points][n_outputs],
+ *   out_grad [n_points][n_outputs][n_vars] (or NULL). */
+ivb_status ivb_point_grad(ivb_problem* p, int64_t n_points, const double* x, double* out_f,
+                          double* out_grad, void* cuda_stream);
+
+/* Split counts for one node (host arrays): uniform (Section 3.1.1: N per dim,
+ * N = floor(target^(1/n))), largest (Section 3.1.1: widest dim only) or
+ * adaptive (Section 3.1.2: uniform, then +1 on the dims of largest relative
+ * width per subinterval while the product stays <= target). `ref_widths`
+ * [n] scales widths for "relative" (NULL = absolute). */
+ivb_status ivb_pick_splits(int32_t n, const double* box, const double* ref_widths,
+                           int64_t target, int32_t strategy, int32_t* out_splits);
+
+/* ---------------------------------------------------------------- B&B
+ * Best-first spatial branch and bound (Section 3, Fig. 3) with this
+ * library's Subdomain Lower Bounding as the lower-bounding solver; a
+ * measurement harness for time-to-gap. Each iteration pops up to `batch`
+ * open nodes of lowest lower bound, bisects each along the dimension of
+ * largest width relative to the root box and bounds all children in one
+ * ivb_bound_nodes_ex call. Upper bounds are the certified centre-point
+ * values of ivb_bound_nodes_ex (no local solver). Nodes are dropped when
+ * infeasible or lb >= UB - max(eps_abs, eps_rel |UB|); the run stops when
+ * UB - min(open lb) is within that tolerance or a limit is reached. */
+typedef struct {
+    int32_t batch;             /* nodes popped per iteration (>= 1)         */
+    int32_t split_mode;        /* 0: fixed `splits`; 1 + IVB_SPLIT_*: picker */
+    const int32_t* splits;     /* [n] fixed splits (split_mode 0), host     */
+    int64_t target;            /* subdomains per node for the picker        */
+    double eps_abs, eps_rel;   /* optimality tolerance                      */
+    int64_t max_nodes;         /* limit on bounded nodes (0 = none)         */
+    double time_limit;         /* seconds (0 = none)                        */
+} ivb_bnb_options;
+
+typedef struct {
+    double lb, ub;             /* final global bounds (lb <= min <= ub)     */
+    int64_t iterations;        /* nodes branched                            */
+    int64_t nodes_bounded;
+    int64_t subdomains;        /* subdomains bounded in total               */
+    double seconds;            /* wall clock of the whole solve             */
+    int32_t converged;         /* 1 if the tolerance was met                */
+    int64_t open_nodes;
+} ivb_bnb_result;
+
+void ivb_bnb_options_default(ivb_bnb_options* o);
+/* root: host array [n][2]; n must equal the problem's n_vars. */
+ivb_status ivb_bnb_solve(ivb_problem* p, int32_t n, const double* root, const ivb_bnb_options* opt,
+                         ivb_bnb_result* result, void* cuda_stream);
+
+/* Tuning actually used by the batched path after autotuning (may be NULL):
+ * block threads, blocks per SM, tile, frame in shared (0/1). */
+ivb_status ivb_get_tuning(ivb_problem* p, int32_t* block_threads, int32_t* blocks_per_sm,
+                          int32_t* tile, int32_t* frame_in_shared);
+
+/* Number of kernel launches the library issued on this handle so far. */
+int64_t ivb_launch_count(const ivb_problem* p);
+
+/* Text of the last error on this handle ("" if none); p may be NULL for the
+ * last error of ivb_create_problem on this thread. */
+const char* ivb_last_error(const ivb_problem* p);
+
+/* Release everything the handle owns; NULL is accepted. */
+void ivb_destroy(ivb_problem* p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

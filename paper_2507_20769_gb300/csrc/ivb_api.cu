@@ -1,0 +1,724 @@
+// ivb_api.cu -- the C ABI declared in include/ivb.h: problem handles, input
+// validation, the device node queue, the batched persistent launch replayed as
+// a CUDA graph, the plain one-node-per-launch path, the autotuner, per-subdomain
+// enclosures and point gradients.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ivb.h"
+#include "ivb_internal.h"
+#include "ivb_kernels.h"
+
+namespace ivb {
+std::string validate_tape(const ivb_tape* t);
+std::string compile_tape(const ivb_tape* t, HostProgram& P, std::vector<Ins>& ins, std::vector<RIns>& rins,
+                         std::vector<double>& consts);
+}  // namespace ivb
+
+using namespace ivb;
+
+struct ivb_problem {
+    ivb_options opt{};
+    HostProgram P{};
+    int n = 0, n_out = 0, obj = 0;
+    uint8_t out_kind[64]{};
+    // program on the device
+    ProgDesc* d_prog = nullptr;
+    Ins* d_ins = nullptr;
+    RIns* d_rins = nullptr;
+    double* d_consts = nullptr;
+    uint8_t* d_out_kind = nullptr;
+    // per-call buffers (capacity max_nodes)
+    int max_nodes = 0;
+    int rec_bytes = 0;
+    char* d_queue = nullptr;
+    char* h_queue = nullptr;            // pinned staging of the queue
+    cudaEvent_t queue_free = nullptr;   // the last copy out of h_queue has completed
+    unsigned long long* d_keys = nullptr;
+    unsigned long long* d_counter = nullptr;
+    double *d_lb = nullptr, *d_ub = nullptr, *d_minlo = nullptr, *d_maxhi = nullptr;
+    uint8_t* d_inf = nullptr;
+    // frames
+    double* d_frame = nullptr;
+    size_t frame_bytes = 0;
+    // tuning
+    int sm_count = 0, smem_optin = 0;
+    bool tuned = false;       // final configuration chosen
+    bool cfg_ready = false;   // some configuration chosen (defaults while waiting for a batch worth tuning on)
+    int block = 128, bps = 4, tile = 512, frame_smem = 0;
+    // graph of the batched call
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    // point gradients
+    double* d_pframe = nullptr;
+    size_t pframe_bytes = 0;
+    long long launches = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+ivb_status fail(ivb_problem* p, ivb_status st, const std::string& msg) {
+    if (p) p->err = msg;
+    else g_create_error = msg;
+    return st;
+}
+
+ivb_status cuda_fail(ivb_problem* p, cudaError_t e, const char* where) {
+    return fail(p, e == cudaErrorMemoryAllocation ? IVB_ENOMEM : IVB_ECUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                  \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail(p, e_, #call);    \
+    } while (0)
+
+bool is_device_ptr(const void* ptr) {
+    if (!ptr) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) { cudaGetLastError(); return false; }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int kernel_mode(const ivb_problem* p, bool store) {
+    const bool adj = p->opt.grad_mode == IVB_GRAD_ADJOINT;
+    return store ? (adj ? KM_ADJ_STORE : KM_FWD_STORE) : (adj ? KM_ADJ_REDUCE : KM_FWD_REDUCE);
+}
+
+int frame_units(const ivb_problem* p) {
+    return p->opt.grad_mode == IVB_GRAD_ADJOINT ? p->P.L.total_adj : p->P.L.total_fwd;
+}
+
+// Read host or device input arrays into host vectors (device arrays are
+// copied synchronously on the stream: validation needs the values).
+template <class T>
+ivb_status fetch(ivb_problem* p, const T* src, size_t count, std::vector<T>& dst, cudaStream_t s) {
+    dst.resize(count);
+    if (is_device_ptr(src)) {
+        CK(cudaMemcpyAsync(dst.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    } else {
+        std::memcpy(dst.data(), src, count * sizeof(T));
+    }
+    return IVB_OK;
+}
+
+// Validate boxes and splits, write the node queue into the pinned staging
+// buffer; returns the queue size in bytes through *bytes.
+ivb_status stage_queue(ivb_problem* p, int n_nodes, const double* boxes, const int32_t* splits, long long g_begin,
+                       long long g_count, bool enclose, size_t* bytes, long long* total_out, cudaStream_t s) {
+    const int n = p->n;
+    std::vector<double> B;
+    std::vector<int32_t> S;
+    ivb_status st = fetch(p, boxes, (size_t)n_nodes * n * 2, B, s);
+    if (st) return st;
+    st = fetch(p, splits, (size_t)n_nodes * n, S, s);
+    if (st) return st;
+    // the previous call's copy out of the staging buffer must have finished
+    CK(cudaEventSynchronize(p->queue_free));
+    char* q = p->h_queue;
+    long long* hdr = reinterpret_cast<long long*>(q);
+    long long* off = reinterpret_cast<long long*>(q + kQueueHeader);
+    char* recs = q + kQueueHeader + 8 * (size_t)(n_nodes + 1);
+    long long acc = 0;
+    const double lim = std::ldexp(1.0, 1000);
+    for (int nd = 0; nd < n_nodes; ++nd) {
+        double* lo = reinterpret_cast<double*>(recs + (size_t)nd * p->rec_bytes);
+        double* hi = lo + n;
+        double* h = hi + n;
+        int32_t* N = reinterpret_cast<int32_t*>(h + n);
+        long long cnt = 1;
+        for (int i = 0; i < n; ++i) {
+            const double a = B[((size_t)nd * n + i) * 2], b = B[((size_t)nd * n + i) * 2 + 1];
+            const int32_t k = S[(size_t)nd * n + i];
+            if (!std::isfinite(a) || !std::isfinite(b) || !(a <= b))
+                return fail(p, IVB_EINVAL, "node " + std::to_string(nd) + ": box bounds must be finite with lo <= hi");
+            if (std::fabs(a) > lim || std::fabs(b) > lim)
+                return fail(p, IVB_EINVAL, "node " + std::to_string(nd) + ": |box endpoint| exceeds 2^1000");
+            if (k < 1) return fail(p, IVB_EINVAL, "node " + std::to_string(nd) + ": splits must be >= 1");
+            cnt *= k;
+            if (cnt > (1LL << 31))
+                return fail(p, IVB_EINVAL, "node " + std::to_string(nd) + ": product of splits exceeds 2^31");
+            lo[i] = a;
+            hi[i] = b;
+            h[i] = (b - a) / (double)k;   // RN(RN(hi - lo) / N), as in the subdomain endpoint formula
+            N[i] = k;
+        }
+        off[nd] = acc;
+        acc += cnt;
+    }
+    off[n_nodes] = acc;
+    long long g_end = acc;
+    if (enclose) {
+        if (g_begin < 0 || g_count < 0 || g_begin + g_count > acc)
+            return fail(p, IVB_EINVAL, "subdomain range outside the node");
+        g_end = g_begin + g_count;
+    }
+    hdr[0] = n_nodes;
+    hdr[1] = g_end;
+    *bytes = queue_bytes(n_nodes, n);
+    *total_out = g_end;
+    return IVB_OK;
+}
+
+ivb_status ensure_frame(ivb_problem* p, int grid, int block) {
+    const size_t need = (size_t)grid * block * frame_units(p) * sizeof(double);
+    if (need <= p->frame_bytes) return IVB_OK;
+    if (p->d_frame) cudaFree(p->d_frame);
+    p->d_frame = nullptr;
+    p->frame_bytes = 0;
+    if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
+    CK(cudaMalloc(&p->d_frame, need));
+    p->frame_bytes = need;
+    return IVB_OK;
+}
+
+KParams make_params(ivb_problem* p, int frame_smem) {
+    KParams K{};
+    K.prog = p->d_prog;
+    K.queue = p->d_queue;
+    K.rec_bytes = p->rec_bytes;
+    K.counter = p->d_counter;
+    K.tile = p->tile;
+    K.gframe = p->d_frame;
+    K.frame_in_smem = frame_smem;
+    K.frame_units = frame_units(p);
+    K.keys = p->d_keys;
+    K.form = p->opt.form;
+    return K;
+}
+
+size_t smem_bytes(const ivb_problem* p, int block, int frame_smem) {
+    return frame_smem ? (size_t)block * frame_units(p) * sizeof(double) : 0;
+}
+
+// enqueue: keys, counter, bound kernel, finalize (the batched graph body)
+ivb_status enqueue_bound(ivb_problem* p, int grid, int block, int tile, int frame_smem, int max_nodes, cudaStream_t s) {
+    const int mode = kernel_mode(p, false);
+    CK(launch_init_keys(p->d_keys, p->d_queue, max_nodes, p->n_out, s));
+    CK(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned long long), s));
+    KParams K = make_params(p, frame_smem);
+    K.tile = tile;
+    const size_t sm = smem_bytes(p, block, frame_smem);
+    CK(launch_bound(mode, K, grid, block, sm, s));
+    FinalizeParams F{};
+    F.keys = p->d_keys;
+    F.queue = p->d_queue;
+    F.max_nodes = max_nodes;
+    F.n_out = p->n_out;
+    F.obj = p->obj;
+    F.filter = p->opt.filter;
+    F.out_kind = p->d_out_kind;
+    F.lb = p->d_lb;
+    F.inf = p->d_inf;
+    F.ub = p->d_ub;
+    F.minlo = p->d_minlo;
+    F.maxhi = p->d_maxhi;
+    CK(launch_finalize(F, s));
+    p->launches += 3;
+    return IVB_OK;
+}
+
+struct TuneCand {
+    int block, bps, smem;
+};
+
+// Pick block size, blocks per SM and frame placement by timing the bound
+// kernel on the staged batch (results do not depend on the choice).
+ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
+    const int mode = kernel_mode(p, false);
+    const int fu = frame_units(p);
+    std::vector<TuneCand> cands;
+    const int blocks[] = {64, 128, 256};
+    const int bpss[] = {1, 2, 4, 8};
+    for (int b : blocks)
+        for (int k : bpss) {
+            const int warps = b * k / 32;
+            if (warps < 4 || warps > 32) continue;
+            for (int sm = 0; sm < 2; ++sm) {
+                const size_t bytes = smem_bytes(p, b, sm);
+                if (sm && (bytes + 1024 > (size_t)p->smem_optin || bytes * k > 220 * 1024)) continue;
+                if (p->opt.frame_in_shared == 0 && sm) continue;
+                if (p->opt.frame_in_shared == 1 && !sm) continue;
+                if (occupancy_blocks(mode, b, bytes) < k) continue;
+                cands.push_back({b, k, sm});
+            }
+        }
+    if (cands.empty()) cands.push_back({64, 1, 0});
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    TuneCand bc = cands[0];
+    for (const TuneCand& c : cands) {
+        const int grid = p->sm_count * c.bps;
+        ivb_status st = ensure_frame(p, grid, c.block);
+        if (st) return st;
+        const int tile = c.block * 4;
+        // warm-up + timed run on the staged batch
+        for (int rep = 0; rep < 2; ++rep) {
+            if (rep == 1) CK(cudaEventRecord(e0, s));
+            st = enqueue_bound(p, grid, c.block, tile, c.smem, p->max_nodes, s);
+            if (st) return st;
+        }
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; bc = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    (void)total;
+    p->block = bc.block;
+    p->bps = bc.bps;
+    p->frame_smem = bc.smem;
+    p->tile = bc.block * 4;
+    p->tuned = true;
+    p->cfg_ready = true;
+    if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
+    return IVB_OK;
+}
+
+ivb_status default_tuning(ivb_problem* p) {
+    const int mode = kernel_mode(p, false);
+    p->block = p->opt.block_threads > 0 ? p->opt.block_threads : 128;
+    p->bps = p->opt.blocks_per_sm > 0 ? p->opt.blocks_per_sm : 4;
+    const size_t bytes = smem_bytes(p, p->block, 1);
+    if (p->opt.frame_in_shared == 1) p->frame_smem = 1;
+    else if (p->opt.frame_in_shared == 0) p->frame_smem = 0;
+    else p->frame_smem = (bytes + 1024 <= (size_t)p->smem_optin && bytes * p->bps <= 220 * 1024) ? 1 : 0;
+    const int occ = occupancy_blocks(mode, p->block, smem_bytes(p, p->block, p->frame_smem));
+    if (occ < 1) return fail(p, IVB_ENOTSUP, "launch configuration does not fit on an SM");
+    if (p->bps > occ) p->bps = occ;
+    p->tile = p->opt.tile > 0 ? ((p->opt.tile + p->block - 1) / p->block) * p->block : p->block * 4;
+    p->cfg_ready = true;
+    const bool explicit_cfg = p->opt.block_threads > 0 || p->opt.blocks_per_sm > 0;
+    if (!p->opt.autotune || explicit_cfg) p->tuned = true;
+    return IVB_OK;
+}
+
+// copy node results to the caller (device -> device or device -> host)
+ivb_status deliver(ivb_problem* p, int n_nodes, double* out_lb, uint8_t* out_inf, double* out_ub, double* out_minlo,
+                   double* out_maxhi, cudaStream_t s, bool* host_out) {
+    struct Item { void* dst; const void* src; size_t bytes; };
+    const Item items[] = {
+        {out_lb, p->d_lb, (size_t)n_nodes * sizeof(double)},
+        {out_inf, p->d_inf, (size_t)n_nodes},
+        {out_ub, p->d_ub, (size_t)n_nodes * sizeof(double)},
+        {out_minlo, p->d_minlo, (size_t)n_nodes * p->n_out * sizeof(double)},
+        {out_maxhi, p->d_maxhi, (size_t)n_nodes * p->n_out * sizeof(double)},
+    };
+    for (const Item& it : items) {
+        if (!it.dst) continue;
+        const bool dev = is_device_ptr(it.dst);
+        if (!dev) *host_out = true;
+        CK(cudaMemcpyAsync(it.dst, it.src, it.bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    }
+    return IVB_OK;
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+
+extern "C" void ivb_options_default(ivb_options* o) {
+    if (!o) return;
+    o->grad_mode = IVB_GRAD_ADJOINT;
+    o->form = IVB_FORM_MVF;
+    o->filter = 0;
+    o->batched = 1;
+    o->use_graph = 1;
+    o->autotune = 1;
+    o->block_threads = 0;
+    o->blocks_per_sm = 0;
+    o->tile = 0;
+    o->max_nodes = 4096;
+    o->frame_in_shared = -1;
+}
+
+extern "C" ivb_status ivb_create_problem(const ivb_tape* tape, const ivb_options* opt, ivb_problem** out) {
+    if (!out) return fail(nullptr, IVB_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::string e = validate_tape(tape);
+    if (!e.empty()) return fail(nullptr, IVB_ETAPE, e);
+    ivb_options o;
+    ivb_options_default(&o);
+    if (opt) o = *opt;
+    if (o.grad_mode != IVB_GRAD_FORWARD && o.grad_mode != IVB_GRAD_ADJOINT)
+        return fail(nullptr, IVB_EINVAL, "grad_mode must be IVB_GRAD_FORWARD or IVB_GRAD_ADJOINT");
+    if (o.form < 0 || o.form > 2) return fail(nullptr, IVB_EINVAL, "form must be 0, 1 or 2");
+    if (o.max_nodes < 1 || o.max_nodes > (1 << 20)) return fail(nullptr, IVB_EINVAL, "max_nodes must be in [1, 2^20]");
+    if (o.block_threads < 0 || o.block_threads > 512 || (o.block_threads % 32))
+        return fail(nullptr, IVB_EINVAL, "block_threads must be a multiple of 32 up to 512 (0 = auto)");
+    ivb_problem* p = new ivb_problem();
+    p->opt = o;
+    std::vector<Ins> ins;
+    std::vector<RIns> rins;
+    std::vector<double> consts;
+    e = compile_tape(tape, p->P, ins, rins, consts);
+    if (!e.empty()) { delete p; return fail(nullptr, IVB_ENOTSUP, e); }
+    p->n = tape->n_vars;
+    p->n_out = tape->n_outputs;
+    p->obj = p->P.obj;
+    for (int i = 0; i < p->n_out; ++i) p->out_kind[i] = tape->out_kind[i];
+    p->max_nodes = o.max_nodes;
+    p->rec_bytes = queue_rec_bytes(p->n);
+
+    auto bail = [&](cudaError_t ce, const char* where) {
+        std::string m = std::string(where) + ": " + cudaGetErrorString(ce);
+        ivb_destroy(p);
+        return fail(nullptr, ce == cudaErrorMemoryAllocation ? IVB_ENOMEM : IVB_ECUDA, m);
+    };
+#define CKC(call)                                   \
+    do {                                            \
+        cudaError_t e_ = (call);                    \
+        if (e_ != cudaSuccess) return bail(e_, #call); \
+    } while (0)
+    int dev = 0;
+    CKC(cudaGetDevice(&dev));
+    CKC(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    CKC(cudaDeviceGetAttribute(&p->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    for (int m = 0; m < 4; ++m) CKC(set_bound_smem_limit(m, p->smem_optin));
+
+    CKC(cudaMalloc(&p->d_ins, std::max<size_t>(1, ins.size()) * sizeof(Ins)));
+    CKC(cudaMalloc(&p->d_rins, std::max<size_t>(1, rins.size()) * sizeof(RIns)));
+    CKC(cudaMalloc(&p->d_consts, std::max<size_t>(1, consts.size()) * sizeof(double)));
+    if (!ins.empty()) CKC(cudaMemcpy(p->d_ins, ins.data(), ins.size() * sizeof(Ins), cudaMemcpyHostToDevice));
+    if (!rins.empty()) CKC(cudaMemcpy(p->d_rins, rins.data(), rins.size() * sizeof(RIns), cudaMemcpyHostToDevice));
+    if (!consts.empty())
+        CKC(cudaMemcpy(p->d_consts, consts.data(), consts.size() * sizeof(double), cudaMemcpyHostToDevice));
+    ProgDesc D{};
+    D.ins = p->d_ins;
+    D.rins = p->d_rins;
+    D.consts = p->d_consts;
+    D.n = p->n;
+    D.n_out = p->n_out;
+    D.obj = p->obj;
+    D.has_eq = p->P.has_eq;
+    D.pt_begin = p->P.pt_begin;
+    D.pt_count = p->P.pt_count;
+    D.tan_begin = p->P.tan_begin;
+    D.tan_count = p->P.tan_count;
+    for (int i = 0; i < p->n_out; ++i) {
+        D.pt_out_ref[i] = (uint32_t)p->P.pt_out_ref[i];
+        D.pt_out_kind[i] = (uint32_t)p->P.pt_out_kind[i];
+        D.tan_out_ref[i] = (uint32_t)p->P.tan_out_ref[i];
+        D.tan_out_kind[i] = (uint32_t)p->P.tan_out_kind[i];
+        D.adj[i] = p->P.adj[i];
+        D.out_kind[i] = p->out_kind[i];
+    }
+    D.L = p->P.L;
+    CKC(cudaMalloc(&p->d_prog, sizeof(ProgDesc)));
+    CKC(cudaMemcpy(p->d_prog, &D, sizeof(ProgDesc), cudaMemcpyHostToDevice));
+    CKC(cudaMalloc(&p->d_out_kind, 64));
+    CKC(cudaMemcpy(p->d_out_kind, p->out_kind, 64, cudaMemcpyHostToDevice));
+
+    const size_t qb = queue_bytes(p->max_nodes, p->n);
+    CKC(cudaMalloc(&p->d_queue, qb));
+    CKC(cudaMallocHost(&p->h_queue, qb));
+    CKC(cudaEventCreateWithFlags(&p->queue_free, cudaEventDisableTiming));
+    CKC(cudaEventRecord(p->queue_free, 0));
+    CKC(cudaMalloc(&p->d_keys, (size_t)p->max_nodes * (2 * p->n_out + 2) * sizeof(unsigned long long)));
+    CKC(cudaMalloc(&p->d_counter, sizeof(unsigned long long)));
+    CKC(cudaMalloc(&p->d_lb, (size_t)p->max_nodes * sizeof(double)));
+    CKC(cudaMalloc(&p->d_ub, (size_t)p->max_nodes * sizeof(double)));
+    CKC(cudaMalloc(&p->d_inf, (size_t)p->max_nodes));
+    CKC(cudaMalloc(&p->d_minlo, (size_t)p->max_nodes * p->n_out * sizeof(double)));
+    CKC(cudaMalloc(&p->d_maxhi, (size_t)p->max_nodes * p->n_out * sizeof(double)));
+    CKC(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+#undef CKC
+    *out = p;
+    return IVB_OK;
+}
+
+extern "C" ivb_status ivb_bound_nodes_ex(ivb_problem* p, int32_t n_nodes, const double* boxes,
+                                         const int32_t* splits_per_dim, double* out_lb, uint8_t* out_infeasible,
+                                         double* out_ub, double* out_minlo, double* out_maxhi, void* cuda_stream) {
+    if (!p) return fail(nullptr, IVB_EINVAL, "problem handle is NULL");
+    p->err.clear();
+    if (n_nodes == 0) return IVB_OK;   // empty batch: nothing to bound
+    if (n_nodes < 0 || n_nodes > p->max_nodes)
+        return fail(p, IVB_EINVAL, "n_nodes must be in [0, max_nodes]");
+    if (!boxes || !splits_per_dim) return fail(p, IVB_EINVAL, "boxes and splits_per_dim must not be NULL");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    size_t qbytes = 0;
+    long long total = 0;
+    ivb_status st = stage_queue(p, n_nodes, boxes, splits_per_dim, 0, 0, false, &qbytes, &total, s);
+    if (st) return st;
+    bool host_out = false;
+
+    if (!p->opt.batched) {
+        // plain path: one node per launch, node queue of one record each
+        if (!p->cfg_ready) { st = default_tuning(p); if (st) return st; }
+        const int n = p->n;
+        std::vector<char> one(queue_bytes(1, n));
+        const char* q = p->h_queue;
+        const long long* off = reinterpret_cast<const long long*>(q + kQueueHeader);
+        const char* recs = q + kQueueHeader + 8 * (size_t)(n_nodes + 1);
+        for (int nd = 0; nd < n_nodes; ++nd) {
+            // build a one-node queue in place at the front of the device buffer
+            long long hdr[2] = {1, off[nd + 1] - off[nd]};
+            long long o2[2] = {0, off[nd + 1] - off[nd]};
+            std::memset(one.data(), 0, kQueueHeader);
+            std::memcpy(one.data(), hdr, sizeof(hdr));
+            std::memcpy(one.data() + kQueueHeader, o2, sizeof(o2));
+            std::memcpy(one.data() + kQueueHeader + 16, recs + (size_t)nd * p->rec_bytes, p->rec_bytes);
+            CK(cudaMemcpyAsync(p->d_queue, one.data(), one.size(), cudaMemcpyHostToDevice, s));
+            const long long S = o2[1];
+            const long long tiles = (S + p->block - 1) / p->block;
+            const int grid = (int)std::min<long long>(tiles, (long long)p->sm_count * p->bps);
+            st = ensure_frame(p, grid, p->block);
+            if (st) return st;
+            const int mode = kernel_mode(p, false);
+            CK(launch_init_keys(p->d_keys, p->d_queue, 1, p->n_out, s));
+            CK(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned long long), s));
+            KParams K = make_params(p, p->frame_smem);
+            K.tile = p->block;
+            CK(launch_bound(mode, K, grid, p->block, smem_bytes(p, p->block, p->frame_smem), s));
+            FinalizeParams F{};
+            F.keys = p->d_keys; F.queue = p->d_queue; F.max_nodes = 1; F.n_out = p->n_out; F.obj = p->obj;
+            F.filter = p->opt.filter; F.out_kind = p->d_out_kind;
+            F.lb = p->d_lb + nd; F.inf = p->d_inf + nd; F.ub = p->d_ub + nd;
+            F.minlo = p->d_minlo + (size_t)nd * p->n_out; F.maxhi = p->d_maxhi + (size_t)nd * p->n_out;
+            CK(launch_finalize(F, s));
+            p->launches += 3;
+            // the host buffer `one` is reused: wait for this node's copy
+            CK(cudaStreamSynchronize(s));
+        }
+        CK(cudaEventRecord(p->queue_free, s));
+    } else {
+        CK(cudaMemcpyAsync(p->d_queue, p->h_queue, qbytes, cudaMemcpyHostToDevice, s));
+        CK(cudaEventRecord(p->queue_free, s));
+        if (!p->tuned) {
+            // tune on the first batch with enough work to time; defaults until then
+            const bool explicit_cfg = p->opt.block_threads > 0 || p->opt.blocks_per_sm > 0;
+            if (p->opt.autotune && !explicit_cfg && total >= (1LL << 18)) st = autotune(p, total, s);
+            else if (!p->cfg_ready) st = default_tuning(p);
+            if (st) return st;
+        }
+        const int grid = p->sm_count * p->bps;
+        st = ensure_frame(p, grid, p->block);
+        if (st) return st;
+        if (p->opt.use_graph) {
+            if (!p->gexec) {
+                cudaGraph_t g = nullptr;
+                CK(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+                st = enqueue_bound(p, grid, p->block, p->tile, p->frame_smem, p->max_nodes, p->cap_stream);
+                cudaGraph_t gg = nullptr;
+                cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &gg);
+                if (st) { if (gg) cudaGraphDestroy(gg); return st; }
+                if (ce != cudaSuccess) return cuda_fail(p, ce, "cudaStreamEndCapture");
+                g = gg;
+                ce = cudaGraphInstantiate(&p->gexec, g, 0);
+                cudaGraphDestroy(g);
+                if (ce != cudaSuccess) { p->gexec = nullptr; return cuda_fail(p, ce, "cudaGraphInstantiate"); }
+                p->launches -= 3;   // captured, not launched
+            }
+            CK(cudaGraphLaunch(p->gexec, s));
+            p->launches += 3;
+        } else {
+            st = enqueue_bound(p, grid, p->block, p->tile, p->frame_smem, p->max_nodes, s);
+            if (st) return st;
+        }
+    }
+    st = deliver(p, n_nodes, out_lb, out_infeasible, out_ub, out_minlo, out_maxhi, s, &host_out);
+    if (st) return st;
+    if (host_out) CK(cudaStreamSynchronize(s));
+    return IVB_OK;
+}
+
+extern "C" ivb_status ivb_bound_nodes(ivb_problem* p, int32_t n_nodes, const double* boxes,
+                                      const int32_t* splits_per_dim, double* out_lb, uint8_t* out_infeasible,
+                                      void* cuda_stream) {
+    return ivb_bound_nodes_ex(p, n_nodes, boxes, splits_per_dim, out_lb, out_infeasible, nullptr, nullptr, nullptr,
+                              cuda_stream);
+}
+
+extern "C" ivb_status ivb_enclose(ivb_problem* p, const double* box, const int32_t* splits_per_dim, int64_t first,
+                                  int64_t count, double* out_F, double* out_Fc, double* out_G, void* cuda_stream) {
+    if (!p) return fail(nullptr, IVB_EINVAL, "problem handle is NULL");
+    p->err.clear();
+    if (!box || !splits_per_dim || !out_F) return fail(p, IVB_EINVAL, "box, splits and out_F must not be NULL");
+    if (count < 1 || count > (1LL << 24)) return fail(p, IVB_EINVAL, "count must be in [1, 2^24]");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    size_t qbytes = 0;
+    long long total = 0;
+    ivb_status st = stage_queue(p, 1, box, splits_per_dim, first, count, true, &qbytes, &total, s);
+    if (st) return st;
+    if (!p->cfg_ready) { st = default_tuning(p); if (st) return st; }
+    CK(cudaMemcpyAsync(p->d_queue, p->h_queue, qbytes, cudaMemcpyHostToDevice, s));
+    CK(cudaEventRecord(p->queue_free, s));
+    const int n_out = p->n_out, n = p->n;
+    const size_t fb = (size_t)count * n_out * 2 * sizeof(double), gb = fb * n;
+    // outputs: written directly when device pointers, else through device temporaries
+    const bool dF = is_device_ptr(out_F), dFc = out_Fc && is_device_ptr(out_Fc), dG = out_G && is_device_ptr(out_G);
+    double *tF = nullptr, *tFc = nullptr, *tG = nullptr;
+    if (!dF) CK(cudaMallocAsync(&tF, fb, s));
+    if (out_Fc && !dFc) CK(cudaMallocAsync(&tFc, fb, s));
+    if (out_G && !dG) CK(cudaMallocAsync(&tG, gb, s));
+    const unsigned long long first_u = (unsigned long long)first;
+    CK(cudaMemcpyAsync(p->d_counter, &first_u, sizeof(first_u), cudaMemcpyHostToDevice, s));
+    const long long tiles = (count + p->block - 1) / p->block;
+    const int grid = (int)std::min<long long>(tiles, (long long)p->sm_count * p->bps);
+    st = ensure_frame(p, grid, p->block);
+    if (st) return st;
+    KParams K = make_params(p, p->frame_smem);
+    K.tile = p->block;
+    K.outF = dF ? out_F : tF;
+    K.outFc = out_Fc ? (dFc ? out_Fc : tFc) : nullptr;
+    K.outG = out_G ? (dG ? out_G : tG) : nullptr;
+    K.store_first_g = first;
+    CK(launch_bound(kernel_mode(p, true), K, grid, p->block, smem_bytes(p, p->block, p->frame_smem), s));
+    p->launches += 1;
+    if (!dF) CK(cudaMemcpyAsync(out_F, tF, fb, cudaMemcpyDeviceToHost, s));
+    if (out_Fc && !dFc) CK(cudaMemcpyAsync(out_Fc, tFc, fb, cudaMemcpyDeviceToHost, s));
+    if (out_G && !dG) CK(cudaMemcpyAsync(out_G, tG, gb, cudaMemcpyDeviceToHost, s));
+    if (tF) CK(cudaFreeAsync(tF, s));
+    if (tFc) CK(cudaFreeAsync(tFc, s));
+    if (tG) CK(cudaFreeAsync(tG, s));
+    // the counter copy reads the stack variable first_u: wait before returning
+    CK(cudaStreamSynchronize(s));
+    return IVB_OK;
+}
+
+extern "C" ivb_status ivb_point_grad(ivb_problem* p, int64_t n_points, const double* x, double* out_f,
+                                     double* out_grad, void* cuda_stream) {
+    if (!p) return fail(nullptr, IVB_EINVAL, "problem handle is NULL");
+    p->err.clear();
+    if (n_points < 1 || !x || !out_f) return fail(p, IVB_EINVAL, "n_points >= 1, x and out_f are required");
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int n = p->n, n_out = p->n_out;
+    const bool dx = is_device_ptr(x), df = is_device_ptr(out_f), dg = out_grad && is_device_ptr(out_grad);
+    const size_t xb = (size_t)n_points * n * sizeof(double), fb = (size_t)n_points * n_out * sizeof(double),
+                 gb = fb * n;
+    double *tx = nullptr, *tf = nullptr, *tg = nullptr;
+    if (!dx) { CK(cudaMallocAsync(&tx, xb, s)); CK(cudaMemcpyAsync(tx, x, xb, cudaMemcpyHostToDevice, s)); }
+    if (!df) CK(cudaMallocAsync(&tf, fb, s));
+    if (out_grad && !dg) CK(cudaMallocAsync(&tg, gb, s));
+    int units = 0;
+    for (int o = 0; o < n_out; ++o)
+        units = std::max(units, n + p->P.adj[o].adj_slots + p->P.adj[o].tape_records);
+    const int block = 128;
+    const int grid = (int)std::min<long long>((n_points + block - 1) / block, (long long)p->sm_count * 8);
+    const size_t need = (size_t)grid * block * std::max(units, 1) * sizeof(double);
+    if (need > p->pframe_bytes) {
+        if (p->d_pframe) CK(cudaFree(p->d_pframe));
+        p->d_pframe = nullptr;
+        p->pframe_bytes = 0;
+        CK(cudaMalloc(&p->d_pframe, need));
+        p->pframe_bytes = need;
+    }
+    CK(launch_point_grad(p->d_prog, n, n_out, std::max(units, 1), n_points, dx ? x : tx, df ? out_f : tf,
+                         out_grad ? (dg ? out_grad : tg) : nullptr, p->d_pframe, grid, block, s));
+    p->launches += 1;
+    if (!df) CK(cudaMemcpyAsync(out_f, tf, fb, cudaMemcpyDeviceToHost, s));
+    if (out_grad && !dg) CK(cudaMemcpyAsync(out_grad, tg, gb, cudaMemcpyDeviceToHost, s));
+    if (tx) CK(cudaFreeAsync(tx, s));
+    if (tf) CK(cudaFreeAsync(tf, s));
+    if (tg) CK(cudaFreeAsync(tg, s));
+    if (!dx || !df || (out_grad && !dg)) CK(cudaStreamSynchronize(s));
+    return IVB_OK;
+}
+
+extern "C" ivb_status ivb_pick_splits(int32_t n, const double* box, const double* ref_widths, int64_t target,
+                                      int32_t strategy, int32_t* out) {
+    if (n < 1 || n > IVB_MAX_VARS || !box || !out || target < 1)
+        return fail(nullptr, IVB_EINVAL, "pick_splits: n in [1,32], box, out and target >= 1 required");
+    if (strategy < 0 || strategy > 2) return fail(nullptr, IVB_EINVAL, "pick_splits: unknown strategy");
+    double w[IVB_MAX_VARS];
+    for (int i = 0; i < n; ++i) {
+        const double wi = box[2 * i + 1] - box[2 * i];
+        w[i] = ref_widths ? (ref_widths[i] > 0 ? wi / ref_widths[i] : 0.0) : wi;
+    }
+    if (strategy == IVB_SPLIT_LARGEST) {
+        int wi = 0;
+        for (int i = 1; i < n; ++i) if (w[i] > w[wi]) wi = i;
+        for (int i = 0; i < n; ++i) out[i] = 1;
+        out[wi] = (int32_t)std::min<int64_t>(target, 2147483647);
+        return IVB_OK;
+    }
+    // largest N with N^n <= target
+    int64_t N = 1;
+    for (;;) {
+        const int64_t M = N + 1;
+        int64_t prod = 1;
+        bool over = false;
+        for (int i = 0; i < n && !over; ++i) {
+            if (prod > target / M) over = true;
+            else prod *= M;
+        }
+        if (over || prod > target) break;
+        N = M;
+    }
+    for (int i = 0; i < n; ++i) out[i] = (int32_t)N;
+    if (strategy == IVB_SPLIT_ADAPTIVE) {
+        int64_t prod = 1;
+        for (int i = 0; i < n; ++i) prod *= out[i];
+        for (;;) {
+            int best = -1;
+            double bv = -1.0;
+            for (int i = 0; i < n; ++i) {
+                const int64_t rest = prod / out[i];
+                if (rest > target / (out[i] + 1)) continue;
+                if (rest * (out[i] + 1) > target) continue;
+                const double v = w[i] / out[i];
+                if (v > bv) { bv = v; best = i; }
+            }
+            if (best < 0) break;
+            prod = (prod / out[best]) * (out[best] + 1);
+            out[best] += 1;
+        }
+    }
+    return IVB_OK;
+}
+
+extern "C" ivb_status ivb_get_tuning(ivb_problem* p, int32_t* block_threads, int32_t* blocks_per_sm, int32_t* tile,
+                                     int32_t* frame_in_shared) {
+    if (!p) return fail(nullptr, IVB_EINVAL, "problem handle is NULL");
+    if (block_threads) *block_threads = p->block;
+    if (blocks_per_sm) *blocks_per_sm = p->bps;
+    if (tile) *tile = p->tile;
+    if (frame_in_shared) *frame_in_shared = p->frame_smem;
+    return IVB_OK;
+}
+
+extern "C" int64_t ivb_launch_count(const ivb_problem* p) { return p ? p->launches : 0; }
+
+extern "C" const char* ivb_last_error(const ivb_problem* p) {
+    return p ? p->err.c_str() : g_create_error.c_str();
+}
+
+extern "C" void ivb_destroy(ivb_problem* p) {
+    if (!p) return;
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    if (p->queue_free) { cudaEventSynchronize(p->queue_free); cudaEventDestroy(p->queue_free); }
+    cudaFree(p->d_prog);
+    cudaFree(p->d_ins);
+    cudaFree(p->d_rins);
+    cudaFree(p->d_consts);
+    cudaFree(p->d_out_kind);
+    cudaFree(p->d_queue);
+    if (p->h_queue) cudaFreeHost(p->h_queue);
+    cudaFree(p->d_keys);
+    cudaFree(p->d_counter);
+    cudaFree(p->d_lb);
+    cudaFree(p->d_ub);
+    cudaFree(p->d_inf);
+    cudaFree(p->d_minlo);
+    cudaFree(p->d_maxhi);
+    cudaFree(p->d_frame);
+    cudaFree(p->d_pframe);
+    delete p;
+}

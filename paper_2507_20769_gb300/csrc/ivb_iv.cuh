@@ -1,0 +1,167 @@
+// ivb_iv.cuh -- outward-rounded binary64 interval arithmetic for sm_103a.
+//
+// Natural interval extensions of the intrinsics (Section 2.2) with directed
+// rounding from the CUDA rounding-mode intrinsics (__dadd_rd / __dmul_ru /
+// __ddiv_rd / __dsqrt_ru / __drcp_rd ...; Section 3.2 notes that basic
+// operations support all rounding modes on the GPU), and two-ulp outward
+// widening of exp/log, whose documented error is one ulp.
+//
+// GB300 has a narrow FP64 pipe (one warp instruction per 64 cycles per SM
+// sub-partition) while the integer pipes are wide, so everything that is not
+// a rounded endpoint operation runs on integers: sign and zero tests, min and
+// max (ordered-integer compares of the bit patterns), negation, neighbour
+// steps. Products pick their endpoint pair by sign case, so an interval
+// product costs two directed multiplies (four only when both factors contain
+// zero in their interior).
+#pragma once
+#include <cstdint>
+
+namespace ivb {
+
+struct iv {
+    double lo, hi;
+};
+
+__device__ __forceinline__ long long bits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ double from_bits(long long b) { return __longlong_as_double(b); }
+
+// x >= 0 (includes -0), x <= 0 (includes +0), x == 0 (either sign); no NaNs
+__device__ __forceinline__ bool ge0(double x) {
+    long long b = bits(x);
+    return b >= 0 || b == (long long)0x8000000000000000ULL;
+}
+__device__ __forceinline__ bool le0(double x) { return bits(x) <= 0; }
+__device__ __forceinline__ bool is0(double x) { return (bits(x) << 1) == 0; }
+__device__ __forceinline__ bool gt0(double x) { return bits(x) > 0; }              // x > 0
+__device__ __forceinline__ bool lt0(double x) {                                    // x < 0
+    long long b = bits(x);
+    return b < 0 && b != (long long)0x8000000000000000ULL;
+}
+__device__ __forceinline__ bool isinf_(double x) { return (bits(x) << 1) == (long long)0xFFE0000000000000ULL; }
+__device__ __forceinline__ bool isnan_(double x) {
+    return (unsigned long long)(bits(x) << 1) > 0xFFE0000000000000ULL;
+}
+
+// monotone signed key: key(x) < key(y) <=> x < y (with -0 < +0)
+__device__ __forceinline__ long long okey(double x) {
+    long long b = bits(x);
+    return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+}
+__device__ __forceinline__ double imin(double x, double y) { return okey(x) <= okey(y) ? x : y; }
+__device__ __forceinline__ double imax(double x, double y) { return okey(x) >= okey(y) ? x : y; }
+__device__ __forceinline__ bool ilt(double x, double y) { return okey(x) < okey(y); }
+__device__ __forceinline__ double ineg(double x) { return from_bits(bits(x) ^ (long long)0x8000000000000000ULL); }
+
+// neighbour towards +inf / -inf (integer steps on the bit pattern)
+__device__ __forceinline__ double next_up(double y) {
+    long long b = bits(y);
+    if (b == 0x7FF0000000000000LL) return y;          // +inf stays
+    if ((b << 1) == 0) return from_bits(1);           // +-0 -> smallest subnormal
+    return from_bits(b >= 0 ? b + 1 : b - 1);
+}
+__device__ __forceinline__ double next_dn(double y) { return ineg(next_up(ineg(y))); }
+
+// ---------------------------------------------------------------- endpoints
+__device__ __forceinline__ double add_dn(double x, double y) { return __dadd_rd(x, y); }
+__device__ __forceinline__ double add_up(double x, double y) { return __dadd_ru(x, y); }
+__device__ __forceinline__ double sub_dn(double x, double y) { return __dsub_rd(x, y); }
+__device__ __forceinline__ double sub_up(double x, double y) { return __dsub_ru(x, y); }
+
+// products with 0 * inf = 0 (interval factors are sets of reals)
+__device__ __forceinline__ double prod_dn(double x, double y) {
+    double p = __dmul_rd(x, y);
+    return (is0(x) || is0(y)) ? 0.0 : p;
+}
+__device__ __forceinline__ double prod_up(double x, double y) {
+    double p = __dmul_ru(x, y);
+    return (is0(x) || is0(y)) ? 0.0 : p;
+}
+
+// ---------------------------------------------------------------- intervals
+__device__ __forceinline__ iv mk(double lo, double hi) { iv r; r.lo = lo; r.hi = hi; return r; }
+__device__ __forceinline__ iv entire() { return mk(-__longlong_as_double(0x7FF0000000000000LL), __longlong_as_double(0x7FF0000000000000LL)); }
+__device__ __forceinline__ iv zero() { return mk(0.0, 0.0); }
+__device__ __forceinline__ iv one() { return mk(1.0, 1.0); }
+__device__ __forceinline__ bool has_inf(iv x) { return isinf_(x.lo) || isinf_(x.hi); }
+
+__device__ __forceinline__ iv iv_add(iv x, iv y) { return mk(add_dn(x.lo, y.lo), add_up(x.hi, y.hi)); }
+__device__ __forceinline__ iv iv_sub(iv x, iv y) { return mk(sub_dn(x.lo, y.hi), sub_up(x.hi, y.lo)); }
+__device__ __forceinline__ iv iv_neg(iv x) { return mk(ineg(x.hi), ineg(x.lo)); }
+
+// product: sign-case choice of the endpoint pairs that realise min and max of
+// the four endpoint products (P: lo >= 0, N: hi <= 0, M: otherwise)
+__device__ __forceinline__ iv iv_mul(iv x, iv y) {
+    const bool xP = ge0(x.lo), xN = !xP && le0(x.hi), xM = !xP && !xN;
+    const bool yP = ge0(y.lo), yN = !yP && le0(y.hi), yM = !yP && !yN;
+    if (xM && yM) {
+        double lo = imin(prod_dn(x.lo, y.hi), prod_dn(x.hi, y.lo));
+        double hi = imax(prod_up(x.lo, y.lo), prod_up(x.hi, y.hi));
+        return mk(lo, hi);
+    }
+    // endpoint pairs (lower | upper):
+    //   P,P: lo*lo | hi*hi   P,M: hi*lo | hi*hi   P,N: hi*lo | lo*hi
+    //   M,P: lo*hi | hi*hi   M,N: hi*lo | lo*lo
+    //   N,P: lo*hi | hi*lo   N,M: lo*hi | lo*lo   N,N: hi*hi | lo*lo
+    const double lx = (xP ? !yP : yN) ? x.hi : x.lo;
+    const double ly = (xP || (xM && yN)) ? y.lo : y.hi;
+    const double ux = (xP ? !yN : yP) ? x.hi : x.lo;
+    const double uy = (xP || (xM && yP)) ? y.hi : y.lo;
+    (void)yM;
+    return mk(prod_dn(lx, ly), prod_up(ux, uy));
+}
+
+__device__ __forceinline__ iv iv_twice(iv x) { return mk(__dmul_rd(2.0, x.lo), __dmul_ru(2.0, x.hi)); }
+
+__device__ __forceinline__ iv iv_sqr(iv x) {
+    if (ge0(x.lo)) return mk(prod_dn(x.lo, x.lo), prod_up(x.hi, x.hi));
+    if (le0(x.hi)) return mk(prod_dn(x.hi, x.hi), prod_up(x.lo, x.lo));
+    // straddles zero: upper end from the endpoint of larger magnitude
+    const double m = (bits(x.lo) & 0x7FFFFFFFFFFFFFFFLL) > (bits(x.hi) & 0x7FFFFFFFFFFFFFFFLL) ? x.lo : x.hi;
+    return mk(0.0, prod_up(m, m));
+}
+
+// reciprocal of an interval without 0 (ENTIRE otherwise)
+__device__ __forceinline__ iv iv_recip(iv y) {
+    if (!(gt0(y.lo) || lt0(y.hi))) return entire();
+    return mk(__drcp_rd(y.hi), __drcp_ru(y.lo));
+}
+__device__ __forceinline__ iv iv_recip_pos(iv y) { return gt0(y.lo) ? iv_recip(y) : entire(); }
+
+// quotient for 0 not in y and finite endpoints (ENTIRE otherwise)
+__device__ __forceinline__ iv iv_div(iv x, iv y) {
+    const bool ypos = gt0(y.lo), yneg = lt0(y.hi);
+    if (!(ypos || yneg) || has_inf(x) || has_inf(y)) return entire();
+    // for y < 0 use x/y = (-x)/(-y) with -y > 0 (negations are exact)
+    double xl = x.lo, xh = x.hi, yl = y.lo, yh = y.hi;
+    if (yneg) { xl = ineg(x.hi); xh = ineg(x.lo); yl = ineg(y.hi); yh = ineg(y.lo); }
+    const double dl = ge0(xl) ? yh : yl;
+    const double dh = ge0(xh) ? yl : yh;
+    return mk(__ddiv_rd(xl, dl), __ddiv_ru(xh, dh));
+}
+
+__device__ __forceinline__ iv iv_sqrt(iv x) {
+    if (lt0(x.lo)) return entire();
+    return mk(__dsqrt_rd(x.lo), __dsqrt_ru(x.hi));
+}
+
+// exp / log: CUDA's double exp and log are within one ulp; two neighbour
+// steps outward enclose the true value also where the spacing of doubles
+// changes between the result and the true value (binade boundaries).
+__device__ __forceinline__ double exp_dn(double x) {
+    double r = next_dn(next_dn(exp(x)));
+    return lt0(r) ? 0.0 : r;
+}
+__device__ __forceinline__ double exp_up(double x) { return next_up(next_up(exp(x))); }
+__device__ __forceinline__ double log_dn(double x) { return next_dn(next_dn(log(x))); }
+__device__ __forceinline__ double log_up(double x) { return next_up(next_up(log(x))); }
+
+__device__ __forceinline__ iv iv_exp(iv x) { return mk(exp_dn(x.lo), exp_up(x.hi)); }
+__device__ __forceinline__ iv iv_log(iv x) {
+    if (!gt0(x.lo)) return entire();
+    return mk(log_dn(x.lo), log_up(x.hi));
+}
+
+// intersection of two enclosures of the same quantity
+__device__ __forceinline__ iv iv_meet(iv x, iv y) { return mk(imax(x.lo, y.lo), imin(x.hi, y.hi)); }
+
+}  // namespace ivb

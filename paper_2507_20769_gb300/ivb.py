@@ -1,0 +1,311 @@
+"""Thin ctypes binding of libivb.so, the C ABI in include/ivb.h.
+
+Argument marshalling only: every step of the bounding runs in the library's
+CUDA kernels. Arrays may be numpy arrays (host) or torch tensors (host or CUDA);
+the library detects the pointer kind. CUDA tensors are processed on torch's
+current stream. Importing this module fails loudly if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+IVB_OK, IVB_EINVAL, IVB_ENOMEM, IVB_ECUDA, IVB_ETAPE, IVB_ETIMEOUT, IVB_ENOTSUP = range(7)
+STATUS_NAMES = {0: "IVB_OK", 1: "IVB_EINVAL", 2: "IVB_ENOMEM", 3: "IVB_ECUDA", 4: "IVB_ETAPE",
+                5: "IVB_ETIMEOUT", 6: "IVB_ENOTSUP"}
+IVB_GRAD_FORWARD, IVB_GRAD_ADJOINT = 0, 1
+IVB_FORM_MVF, IVB_FORM_NIE, IVB_FORM_MVF_NIE = 0, 1, 2
+IVB_SPLIT_UNIFORM, IVB_SPLIT_LARGEST, IVB_SPLIT_ADAPTIVE = 0, 1, 2
+GRAD = {"forward": IVB_GRAD_FORWARD, "adjoint": IVB_GRAD_ADJOINT}
+FORM = {"mvf": IVB_FORM_MVF, "nie": IVB_FORM_NIE, "mvf_nie": IVB_FORM_MVF_NIE}
+SPLIT = {"uniform": IVB_SPLIT_UNIFORM, "largest": IVB_SPLIT_LARGEST, "adaptive": IVB_SPLIT_ADAPTIVE}
+
+
+class IvbError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class ivb_options(ctypes.Structure):
+    _fields_ = [("grad_mode", ctypes.c_int32), ("form", ctypes.c_int32), ("filter", ctypes.c_int32),
+                ("batched", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("max_nodes", ctypes.c_int32), ("frame_in_shared", ctypes.c_int32)]
+
+
+class ivb_tape(ctypes.Structure):
+    _fields_ = [("n_vars", ctypes.c_int32), ("n_ops", ctypes.c_int32), ("n_outputs", ctypes.c_int32),
+                ("ops", ctypes.c_void_p), ("out_idx", ctypes.c_void_p), ("out_kind", ctypes.c_void_p)]
+
+
+class ivb_bnb_options(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int32), ("split_mode", ctypes.c_int32), ("splits", ctypes.c_void_p),
+                ("target", ctypes.c_int64), ("eps_abs", ctypes.c_double), ("eps_rel", ctypes.c_double),
+                ("max_nodes", ctypes.c_int64), ("time_limit", ctypes.c_double)]
+
+
+class ivb_bnb_result(ctypes.Structure):
+    _fields_ = [("lb", ctypes.c_double), ("ub", ctypes.c_double), ("iterations", ctypes.c_int64),
+                ("nodes_bounded", ctypes.c_int64), ("subdomains", ctypes.c_int64), ("seconds", ctypes.c_double),
+                ("converged", ctypes.c_int32), ("open_nodes", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libivb.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise IvbError(IVB_ENOTSUP, f"{path} is not built; run paper_2507_20769_gb300.build.build() "
+                                        "(needs the CUDA toolkit)")
+        L = ctypes.CDLL(path)
+        P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        L.ivb_options_default.argtypes = [P]
+        L.ivb_create_problem.argtypes = [P, P, P]
+        L.ivb_bound_nodes.argtypes = [P, I32, P, P, P, P, P]
+        L.ivb_bound_nodes_ex.argtypes = [P, I32, P, P, P, P, P, P, P, P]
+        L.ivb_enclose.argtypes = [P, P, P, I64, I64, P, P, P, P]
+        L.ivb_point_grad.argtypes = [P, I64, P, P, P, P]
+        L.ivb_pick_splits.argtypes = [I32, P, P, I64, I32, P]
+        L.ivb_get_tuning.argtypes = [P, P, P, P, P]
+        L.ivb_launch_count.argtypes = [P]
+        L.ivb_launch_count.restype = I64
+        L.ivb_last_error.argtypes = [P]
+        L.ivb_last_error.restype = ctypes.c_char_p
+        L.ivb_destroy.argtypes = [P]
+        L.ivb_bnb_options_default.argtypes = [P]
+        L.ivb_bnb_solve.argtypes = [P, I32, P, P, P, P]
+        for f in ("ivb_create_problem", "ivb_bound_nodes", "ivb_bound_nodes_ex", "ivb_enclose", "ivb_point_grad",
+                  "ivb_pick_splits", "ivb_get_tuning", "ivb_bnb_solve"):
+            getattr(L, f).restype = I32
+        _lib = L
+    return _lib
+
+
+# ----------------------------------------------------------------- marshalling
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return ctypes.c_void_p(x.data_ptr())
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("arrays must be C-contiguous")
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+def _stream_for(*xs):
+    for x in xs:
+        if x is not None and _is_torch(x) and x.is_cuda:
+            import torch
+            return ctypes.c_void_p(torch.cuda.current_stream(x.device).cuda_stream)
+    return None
+
+
+def _check(status: int, handle=None):
+    if status != IVB_OK:
+        msg = lib().ivb_last_error(handle)
+        raise IvbError(status, msg.decode() if msg else "")
+
+
+def _as(x, dtype):
+    """numpy array of dtype, or a torch tensor checked for dtype"""
+    if _is_torch(x):
+        import torch
+        want = {np.float64: torch.float64, np.int32: torch.int32}[dtype]
+        if x.dtype != want:
+            raise TypeError(f"expected {want}, got {x.dtype}")
+        return x.contiguous()
+    return np.ascontiguousarray(x, dtype=dtype)
+
+
+def _empty_like_kind(ref, shape, dtype):
+    if ref is not None and _is_torch(ref):
+        import torch
+        tdt = {np.float64: torch.float64, np.uint8: torch.uint8}[dtype]
+        return torch.empty(shape, dtype=tdt, device=ref.device)
+    return np.empty(shape, dtype=dtype)
+
+
+# -------------------------------------------------------------------- the ABI
+
+def ivb_options_default(**overrides) -> ivb_options:
+    o = ivb_options()
+    lib().ivb_options_default(ctypes.byref(o))
+    for k, v in overrides.items():
+        if k == "grad_mode" and isinstance(v, str):
+            v = GRAD[v]
+        if k == "form" and isinstance(v, str):
+            v = FORM[v]
+        setattr(o, k, int(v))
+    return o
+
+
+def ivb_create_problem(tape, options: ivb_options | None = None, **overrides) -> "Problem":
+    return Problem(tape, options, **overrides)
+
+
+def ivb_pick_splits(box, target: int, strategy="adaptive", ref_widths=None) -> np.ndarray:
+    box = np.ascontiguousarray(box, dtype=np.float64).reshape(-1, 2)
+    n = box.shape[0]
+    ref = None if ref_widths is None else np.ascontiguousarray(ref_widths, dtype=np.float64)
+    out = np.empty(n, dtype=np.int32)
+    s = SPLIT[strategy] if isinstance(strategy, str) else int(strategy)
+    _check(lib().ivb_pick_splits(n, _ptr(box), _ptr(ref), int(target), s, _ptr(out)))
+    return out
+
+
+def ivb_last_error(problem=None) -> str:
+    h = None if problem is None else problem._h
+    m = lib().ivb_last_error(h)
+    return m.decode() if m else ""
+
+
+class Problem:
+    """An ivb_problem handle (ivb_create_problem / ivb_destroy)."""
+
+    def __init__(self, tape, options: ivb_options | None = None, **overrides):
+        L = lib()
+        if options is None:
+            options = ivb_options_default(**overrides)
+        else:
+            for k, v in overrides.items():
+                setattr(options, k, int(v))
+        self.options = options
+        self.n_vars, self.n_out = int(tape.n_vars), int(tape.out_idx.shape[0])
+        self._recs = tape.records()
+        self._oi = np.ascontiguousarray(tape.out_idx, dtype=np.int32)
+        self._ok = np.ascontiguousarray(tape.out_kind, dtype=np.uint8)
+        t = ivb_tape(self.n_vars, int(self._recs.shape[0]), self.n_out, self._recs.ctypes.data,
+                     self._oi.ctypes.data, self._ok.ctypes.data)
+        h = ctypes.c_void_p()
+        st = L.ivb_create_problem(ctypes.byref(t), ctypes.byref(options), ctypes.byref(h))
+        if st != IVB_OK:
+            raise IvbError(st, L.ivb_last_error(None).decode())
+        self._h = h
+
+    # -- lifecycle
+    def destroy(self):
+        if getattr(self, "_h", None):
+            lib().ivb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.destroy()
+
+    # -- bounding
+    def ivb_bound_nodes_ex(self, boxes, splits, want_ub=True, want_hull=False, out=None, stream=None):
+        boxes = _as(boxes, np.float64)
+        splits = _as(splits, np.int32)
+        nn = int(boxes.shape[0]) if boxes.ndim == 3 else int(np.prod(boxes.shape)) // (2 * self.n_vars)
+        out = out or {}
+        lb = out.get("lb", _empty_like_kind(boxes, (nn,), np.float64))
+        inf = out.get("infeasible", _empty_like_kind(boxes, (nn,), np.uint8))
+        ub = out.get("ub", _empty_like_kind(boxes, (nn,), np.float64)) if want_ub else None
+        mn = _empty_like_kind(boxes, (nn, self.n_out), np.float64) if want_hull else None
+        mx = _empty_like_kind(boxes, (nn, self.n_out), np.float64) if want_hull else None
+        s = stream if stream is not None else _stream_for(boxes, splits, lb)
+        _check(lib().ivb_bound_nodes_ex(self._h, nn, _ptr(boxes), _ptr(splits), _ptr(lb), _ptr(inf), _ptr(ub),
+                                        _ptr(mn), _ptr(mx), s), self._h)
+        r = {"lb": lb, "infeasible": inf}
+        if want_ub:
+            r["ub"] = ub
+        if want_hull:
+            r["minlo"], r["maxhi"] = mn, mx
+        return r
+
+    def ivb_bound_nodes(self, boxes, splits, stream=None):
+        r = self.ivb_bound_nodes_ex(boxes, splits, want_ub=False, stream=stream)
+        return r["lb"], r["infeasible"]
+
+    def ivb_enclose(self, box, splits, first=0, count=None, want_fc=False, want_g=False, device=None):
+        box = _as(box, np.float64)
+        splits = _as(splits, np.int32)
+        if count is None:
+            sp = splits.cpu().numpy() if _is_torch(splits) else splits
+            count = int(np.prod(sp.astype(np.int64))) - int(first)
+        ref = box if _is_torch(box) else None
+        F = _empty_like_kind(ref, (count, self.n_out, 2), np.float64)
+        Fc = _empty_like_kind(ref, (count, self.n_out, 2), np.float64) if want_fc else None
+        G = _empty_like_kind(ref, (count, self.n_out, self.n_vars, 2), np.float64) if want_g else None
+        _check(lib().ivb_enclose(self._h, _ptr(box), _ptr(splits), int(first), int(count), _ptr(F), _ptr(Fc),
+                                 _ptr(G), _stream_for(box, F)), self._h)
+        return F, Fc, G
+
+    def ivb_point_grad(self, x, want_grad=True, stream=None):
+        x = _as(x, np.float64)
+        m = int(x.shape[0])
+        f = _empty_like_kind(x, (m, self.n_out), np.float64)
+        g = _empty_like_kind(x, (m, self.n_out, self.n_vars), np.float64) if want_grad else None
+        s = stream if stream is not None else _stream_for(x)
+        _check(lib().ivb_point_grad(self._h, m, _ptr(x), _ptr(f), _ptr(g), s), self._h)
+        return f, g
+
+    def ivb_bnb_solve(self, root, splits=None, target=0, strategy="adaptive", batch=1, eps_abs=0.0,
+                      eps_rel=1e-3, max_nodes=0, time_limit=0.0):
+        root = np.ascontiguousarray(root, dtype=np.float64)
+        o = ivb_bnb_options()
+        lib().ivb_bnb_options_default(ctypes.byref(o))
+        sp = None
+        if splits is not None:
+            sp = np.ascontiguousarray(splits, dtype=np.int32)
+            o.split_mode, o.splits = 0, sp.ctypes.data
+        else:
+            o.split_mode = 1 + (SPLIT[strategy] if isinstance(strategy, str) else int(strategy))
+            o.target = int(target)
+        o.batch, o.eps_abs, o.eps_rel = int(batch), float(eps_abs), float(eps_rel)
+        o.max_nodes, o.time_limit = int(max_nodes), float(time_limit)
+        r = ivb_bnb_result()
+        _check(lib().ivb_bnb_solve(self._h, self.n_vars, _ptr(root), ctypes.byref(o), ctypes.byref(r), None),
+               self._h)
+        return {"lb": r.lb, "ub": r.ub, "iterations": r.iterations, "nodes": r.nodes_bounded,
+                "subdomains": r.subdomains, "seconds": r.seconds, "converged": bool(r.converged),
+                "open": r.open_nodes}
+
+    def ivb_get_tuning(self):
+        v = [ctypes.c_int32() for _ in range(4)]
+        _check(lib().ivb_get_tuning(self._h, *[ctypes.byref(x) for x in v]), self._h)
+        return {"block_threads": v[0].value, "blocks_per_sm": v[1].value, "tile": v[2].value,
+                "frame_in_shared": v[3].value}
+
+    def ivb_launch_count(self) -> int:
+        return int(lib().ivb_launch_count(self._h))
+
+    def ivb_last_error(self) -> str:
+        return ivb_last_error(self)
+
+    # short aliases
+    bound_nodes = ivb_bound_nodes
+    bound_nodes_ex = ivb_bound_nodes_ex
+    enclose = ivb_enclose
+    point_grad = ivb_point_grad
+    bnb_solve = ivb_bnb_solve
+    get_tuning = ivb_get_tuning
+    launch_count = ivb_launch_count

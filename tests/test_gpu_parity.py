@@ -1,0 +1,358 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle,
+element by element on seeded inputs.
+
+Bar (from the method's arithmetic): tapes with only + - * / sqr sqrt are
+bit-exact in both gradient modes (every directed operation is correctly
+rounded on both sides and the formulas are the same); tapes with exp/log
+must contain the oracle's tight enclosure, within 4 ulps per transcendental
+operation and, for whole tapes, with endpoint distance at most
+max(4 ulps, 1e-10 * scale) where scale = max(|lo|, |hi|, width) of the
+oracle's interval (the GPU widens each exp/log result by two ulps on top of
+CUDA's one-ulp error, the oracle is within one ulp; later operations carry
+these few-ulp differences forward)."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import problems as P
+from paper_2507_20769_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2507_20769_gb300 import build as B  # noqa: E402
+
+B.build()
+from paper_2507_20769_gb300 import ivb  # noqa: E402
+
+DEV = torch.device("cuda:0")
+INF = math.inf
+
+
+def rational_problem(n=3, K=60, n_ineq=2, seed=777):
+    return W.random_problem(n, K, n_ineq, W.OPS_RATIONAL, [[-3, 2]] * n, seed, "rational")
+
+
+def ulps(a, b):
+    """number of doubles between a and b (both finite, same sign handled)"""
+    ia = np.asarray(a, np.float64).view(np.int64)
+    ib = np.asarray(b, np.float64).view(np.int64)
+    ia = np.where(ia < 0, np.int64(-(2 ** 63)) - ia, ia)
+    ib = np.where(ib < 0, np.int64(-(2 ** 63)) - ib, ib)
+    return np.abs(ia - ib)
+
+
+def assert_contains_close(gpu, ref, what=""):
+    """gpu interval contains ref interval, endpoints within the tolerance"""
+    gl, gh, rl, rh = gpu[..., 0], gpu[..., 1], ref[..., 0], ref[..., 1]
+    assert np.all(gl <= rl), f"{what}: lower end not contained"
+    assert np.all(gh >= rh), f"{what}: upper end not contained"
+    fin = np.isfinite(rl) & np.isfinite(rh)
+    scale = np.maximum(np.maximum(np.abs(rl), np.abs(rh)), rh - rl)
+    tol = np.maximum(1e-10 * np.where(fin, scale, 0.0), 0.0)
+    ok_lo = (ulps(gl, rl) <= 4) | (rl - gl <= tol) | ~fin
+    ok_hi = (ulps(gh, rh) <= 4) | (gh - rh <= tol) | ~fin
+    assert np.all(ok_lo) and np.all(ok_hi), f"{what}: endpoints too far from the oracle"
+
+
+# ------------------------------------------------------------ per subdomain
+
+@pytest.mark.parametrize("grad_mode", ["forward", "adjoint"])
+@pytest.mark.parametrize("form", ["mvf", "nie", "mvf_nie"])
+def test_enclose_bit_exact_rational(grad_mode, form):
+    """Steps 1-2 per subdomain: F, f(c) and G equal the oracle's bit for bit
+    (140 subdomains: several 128-thread tiles and a ragged tail)."""
+    t = rational_problem()
+    box = np.array([[-2.5, 1.0], [-1.0, 1.75], [0.5, 2.0]])
+    splits = np.array([5, 4, 7], np.int32)
+    with ivb.Problem(t, grad_mode=grad_mode, form=form) as p:
+        F, Fc, G = p.enclose(box, splits, want_fc=True, want_g=True)
+    Fo, Fco, Go = oracle.enclose(t, box, splits, grad_mode=grad_mode, form=form, tight=True,
+                                 want_fc=True, want_g=True)
+    assert np.array_equal(Fc, Fco)
+    assert np.array_equal(G, Go)
+    assert np.array_equal(F, Fo)
+
+
+@pytest.mark.parametrize("grad_mode", ["forward", "adjoint"])
+def test_enclose_exp_log_contains(grad_mode):
+    t = W.config_tape(2)
+    box = W.bisection_frontier(t.root_box, 8, seed=5)[3]
+    splits = np.array([3, 4, 3, 3], np.int32)
+    with ivb.Problem(t, grad_mode=grad_mode) as p:
+        F, Fc, G = p.enclose(box, splits, want_fc=True, want_g=True)
+    Fo, Fco, Go = oracle.enclose(t, box, splits, grad_mode=grad_mode, tight=True, want_fc=True, want_g=True)
+    assert_contains_close(Fc, Fco, "f(c)")
+    assert_contains_close(G, Go, "gradient")
+    assert_contains_close(F, Fo, "MVF")
+
+
+@pytest.mark.parametrize("fn,lo,hi", [("exp", -30.0, 30.0), ("exp", -740.0, 700.0), ("log", 1e-300, 1e300),
+                                      ("log", 0.25, 4.0)])
+def test_transcendental_op_within_4_ulps(fn, lo, hi):
+    """one exp / log operation on 4096 intervals: contains the oracle's tight
+    enclosure, each end within 4 ulps of it"""
+    Bd = P.Builder(1)
+    x = Bd.x(0)
+    Bd.output(Bd.exp(x) if fn == "exp" else Bd.log(x))
+    t = Bd.tape([[lo, hi]])
+    with ivb.Problem(t, form="nie", grad_mode="forward") as p:
+        F, _, _ = p.enclose(t.root_box, np.array([4096], np.int32))
+    Fo, _, _ = oracle.enclose(t, t.root_box, [4096], form="nie", tight=True)
+    g, r = F[:, 0], Fo[:, 0]
+    assert np.all(g[:, 0] <= r[:, 0]) and np.all(g[:, 1] >= r[:, 1])
+    m = np.isfinite(r[:, 0]) & (r[:, 0] != 0)
+    assert np.all(ulps(g[m, 0], r[m, 0]) <= 4)
+    m = np.isfinite(r[:, 1])
+    assert np.all(ulps(g[m, 1], r[m, 1]) <= 4)
+
+
+def test_domain_violations_give_entire_like_the_oracle():
+    """sqrt of a negative part, log of a non-positive part, division by an
+    interval with zero: ENTIRE, identically on both sides"""
+    Bd = P.Builder(2)
+    x, y = Bd.x(0), Bd.x(1)
+    a = Bd.sqrt(Bd.sub(x, Bd.const(0.5)))
+    b = Bd.div(Bd.const(1.0), y)
+    Bd.output(Bd.add(a, b))
+    t = Bd.tape([[-1.0, 1.0], [-1.0, 1.0]])
+    for gm in ("forward", "adjoint"):
+        with ivb.Problem(t, grad_mode=gm) as p:
+            F, Fc, G = p.enclose(t.root_box, np.array([4, 5], np.int32), want_fc=True, want_g=True)
+        Fo, Fco, Go = oracle.enclose(t, t.root_box, [4, 5], grad_mode=gm, want_fc=True, want_g=True)
+        assert np.array_equal(F, Fo) and np.array_equal(Fc, Fco) and np.array_equal(G, Go)
+        assert np.any(np.isinf(F))
+
+
+# ------------------------------------------------------------------ per node
+
+def ragged_batch(t, n_nodes, seed, max_split=6):
+    rng = np.random.default_rng(seed)
+    boxes = W.bisection_frontier(t.root_box, n_nodes, seed=seed)
+    splits = rng.integers(1, max_split + 1, (n_nodes, t.n_vars)).astype(np.int32)
+    splits[0] = 1                          # S = 1
+    boxes[1, 0, 1] = boxes[1, 0, 0]        # degenerate dimension
+    return boxes, splits
+
+
+@pytest.mark.parametrize("grad_mode", ["forward", "adjoint"])
+@pytest.mark.parametrize("path", ["graph", "nograph", "plain"])
+def test_bound_nodes_bit_exact_rational(grad_mode, path):
+    """Steps 1-3 for a ragged batch (S from 1 to 216 per node, tiles crossing
+    nodes): lb, infeasibility, centre upper bound and every output's hull
+    equal the oracle's bit for bit, on every launch path."""
+    t = rational_problem()
+    boxes, splits = ragged_batch(t, 37, seed=11)
+    opts = dict(grad_mode=grad_mode, use_graph=int(path == "graph"), batched=int(path != "plain"))
+    with ivb.Problem(t, **opts) as p:
+        r = p.bound_nodes_ex(boxes, splits, want_hull=True)
+        r2 = p.bound_nodes_ex(boxes, splits, want_hull=True)      # second call replays the graph
+    ref = oracle.bound_nodes(t, boxes, splits, grad_mode=grad_mode, tight=True)
+    for rr in (r, r2):
+        assert np.array_equal(rr["lb"], ref["lb"])
+        assert np.array_equal(rr["minlo"], ref["minlo"])
+        assert np.array_equal(rr["maxhi"], ref["maxhi"])
+        assert np.array_equal(rr["ub"], ref["ub"])
+        assert np.array_equal(rr["infeasible"].astype(bool), ref["infeasible"])
+
+
+def test_device_and_host_pointers_agree():
+    t = rational_problem()
+    boxes, splits = ragged_batch(t, 20, seed=3)
+    with ivb.Problem(t) as p:
+        rh = p.bound_nodes_ex(boxes, splits, want_hull=True)
+        rd = p.bound_nodes_ex(torch.from_numpy(boxes).to(DEV), torch.from_numpy(splits).to(DEV), want_hull=True)
+        torch.cuda.synchronize()
+    for k in ("lb", "ub", "minlo", "maxhi", "infeasible"):
+        assert np.array_equal(rh[k], rd[k].cpu().numpy()), k
+
+
+@pytest.mark.parametrize("kind", ["feasible", "infeasible", "eq_out", "eq_in"])
+@pytest.mark.parametrize("filt", [0, 1])
+def test_feasibility_filter_and_ub_match_oracle(kind, filt):
+    t = P.constrained_toy(kind)
+    boxes = W.bisection_frontier(t.root_box, 9, seed=2)
+    splits = np.array([[6, 5]] * 9, np.int32)
+    with ivb.Problem(t, filter=filt) as p:
+        r = p.bound_nodes_ex(boxes, splits, want_hull=True)
+    ref = oracle.bound_nodes(t, boxes, splits, filter=bool(filt))
+    assert np.array_equal(r["lb"], ref["lb"])
+    assert np.array_equal(r["infeasible"].astype(bool), ref["infeasible"])
+    assert np.array_equal(r["ub"], ref["ub"])
+
+
+@pytest.mark.parametrize("config", [1, 2, 3])
+def test_bound_nodes_exp_log_configs_contain_oracle(config):
+    """paper-shaped tapes with exp/log: node hulls contain the oracle's"""
+    t = W.config_tape(config)
+    n_nodes = 6
+    boxes = W.bisection_frontier(t.root_box, n_nodes, seed=config)
+    splits = np.full((n_nodes, t.n_vars), 3 if t.n_vars <= 4 else 2, np.int32)
+    with ivb.Problem(t) as p:
+        r = p.bound_nodes_ex(boxes, splits, want_hull=True)
+    ref = oracle.bound_nodes(t, boxes, splits, tight=True)
+    hull = np.stack([r["minlo"], r["maxhi"]], -1)
+    hull_o = np.stack([ref["minlo"], ref["maxhi"]], -1)
+    assert_contains_close(hull, hull_o, "node hull")
+
+
+def test_full_size_config2_sampled():
+    """configuration 2 at full size (16^4 = 65536 subdomains per node, 16 nodes
+    in one batched launch, autotuned): node hull of one node against the oracle,
+    and 256 sampled subdomains of other nodes one by one"""
+    wl = W.config_workload(2)
+    t = wl.tape
+    boxes = W.bisection_frontier(t.root_box, 16, seed=20)
+    splits = np.tile(wl.splits, (16, 1))
+    with ivb.Problem(t) as p:
+        r = p.bound_nodes_ex(boxes, splits, want_hull=True)
+        rng = np.random.default_rng(0)
+        for nd in (5, 11):
+            ks = np.sort(rng.choice(65536, 128, replace=False))
+            for k in ks[:128]:
+                F, _, _ = p.enclose(boxes[nd], wl.splits, first=int(k), count=1)
+                Fo, _, _ = oracle.enclose(t, boxes[nd], wl.splits, first=int(k), count=1, tight=True)
+                assert_contains_close(F, Fo, f"node {nd} subdomain {k}")
+    ref = oracle.bound_nodes(t, boxes[:1], wl.splits, tight=True)
+    hull = np.stack([r["minlo"][:1], r["maxhi"][:1]], -1)
+    assert_contains_close(hull, np.stack([ref["minlo"], ref["maxhi"]], -1), "full-size node 0")
+    assert r["lb"][0] <= ref["lb"][0]
+
+
+# ------------------------------------------------------------- edge cases
+
+def test_invalid_inputs_rejected():
+    t = rational_problem()
+    with ivb.Problem(t, max_nodes=4) as p:
+        good_b = np.array([t.root_box] * 2)
+        good_s = np.ones((2, t.n_vars), np.int32)
+        bad = []
+        b = good_b.copy(); b[0, 0] = [1.0, 0.0]; bad.append((b, good_s))
+        b = good_b.copy(); b[1, 2, 1] = np.nan; bad.append((b, good_s))
+        s = good_s.copy(); s[1, 1] = 0; bad.append((good_b, s))
+        s = good_s.copy(); s[0] = [2048, 2048, 2048]; bad.append((good_b, s))
+        bad.append((np.array([t.root_box] * 5), np.ones((5, t.n_vars), np.int32)))   # > max_nodes
+        for bb, ss in bad:
+            with pytest.raises(ivb.IvbError) as e:
+                p.bound_nodes(bb, ss)
+            assert e.value.status == ivb.IVB_EINVAL
+        # the handle stays usable after errors; an empty batch is a no-op
+        lb, inf = p.bound_nodes(good_b, good_s)
+        assert np.all(np.isfinite(lb))
+        lb0, _ = p.bound_nodes(np.zeros((0, t.n_vars, 2)), np.zeros((0, t.n_vars), np.int32))
+        assert lb0.shape == (0,)
+
+
+def test_single_subdomain_equals_unsplit_mvf():
+    """N = 1 everywhere: the node bound is the MVF on the whole box"""
+    t = rational_problem(seed=5)
+    with ivb.Problem(t) as p:
+        r = p.bound_nodes_ex(t.root_box[None], np.ones((1, t.n_vars), np.int32), want_hull=True)
+        F, _, _ = p.enclose(t.root_box, np.ones(t.n_vars, np.int32))
+    assert np.array_equal(r["minlo"][0], F[0, :, 0])
+    assert np.array_equal(r["maxhi"][0], F[0, :, 1])
+
+
+# ---------------------------------------------------------- point gradients
+
+def test_point_grad_matches_oracle():
+    t = rational_problem()
+    x = W.sample_points(t.root_box, 300, seed=1)
+    with ivb.Problem(t) as p:
+        f, g = p.point_grad(x)
+    for i in range(x.shape[0]):
+        fo, go = oracle.point_grad(t, x[i])
+        assert np.array_equal(f[i], fo) and np.array_equal(g[i], go)
+    t = W.config_tape(4)
+    x = W.sample_points(t.root_box, 64, seed=2)
+    with ivb.Problem(t) as p:
+        f, g = p.point_grad(torch.from_numpy(x).to(DEV))
+        f, g = f.cpu().numpy(), g.cpu().numpy()
+    for i in range(x.shape[0]):
+        fo, go = oracle.point_grad(t, x[i])
+        assert np.allclose(f[i], fo, rtol=1e-12, atol=1e-12)
+        assert np.allclose(g[i], go, rtol=1e-10, atol=1e-12)
+        h = 1e-6 * np.maximum(1.0, np.abs(x[i]))
+        gfd = oracle.central_diff_q(t, x[i], h)
+        assert np.all(np.abs(g[i] - gfd) <= 1e-6 * np.maximum(1.0, np.abs(g[i])))
+
+
+def test_adjoint_contains_sampled_point_gradients_config4():
+    """configuration 4 (n=16, K=400): on a 2^12 subsample of the 2^20
+    subdomains, every interval adjoint contains 64 point gradients sampled in
+    its subdomain (round-to-nearest point gradients, slack 1e-9 relative for
+    their own rounding)."""
+    wl = W.config_workload(4)
+    t = wl.tape
+    S = int(np.prod(wl.splits))
+    rng = np.random.default_rng(4)
+    ks = np.sort(rng.choice(S, 4096, replace=False))
+    with ivb.Problem(t, grad_mode="adjoint") as p:
+        Gs = []
+        for k in ks:
+            _, _, G = p.enclose(t.root_box, wl.splits, first=int(k), count=1, want_g=True)
+            Gs.append(G[0, 0])
+        pts = []
+        for k in ks:
+            X, _ = oracle.decode(t.root_box, wl.splits, int(k))
+            pts.append(rng.uniform(X[:, 0], X[:, 1], (64, t.n_vars)))
+        pts = np.concatenate(pts)
+        _, g = p.point_grad(pts)
+    g = g[:, 0, :].reshape(len(ks), 64, t.n_vars)
+    Gs = np.stack(Gs)
+    slack = 1e-9 * np.maximum(1.0, np.abs(g))
+    assert np.all(g >= Gs[:, None, :, 0] - slack)
+    assert np.all(g <= Gs[:, None, :, 1] + slack)
+
+
+# --------------------------------------------------------------- B&B
+
+def test_bnb_gpu_matches_oracle_tiny():
+    wl = W.config_workload(1)
+    t = wl.tape
+    ref = oracle.bnb(t, splits=wl.splits, eps_abs=wl.gap_abs, eps_rel=0.0, grad_mode="forward", tight=True,
+                     max_nodes=100000)
+    for gm, batched, batch in (("forward", 0, 1), ("adjoint", 1, 8)):
+        with ivb.Problem(t, grad_mode=gm, batched=batched) as p:
+            r = p.bnb_solve(t.root_box, splits=wl.splits, batch=batch, eps_abs=wl.gap_abs, eps_rel=0.0,
+                            max_nodes=100000)
+        assert r["converged"] and ref["converged"]
+        assert r["ub"] - r["lb"] <= wl.gap_abs
+        # both bracket the same minimum
+        assert r["lb"] <= ref["ub"] and ref["lb"] <= r["ub"]
+
+
+def test_bnb_gpu_follows_oracle_trajectory_rational():
+    """bit-exact bounds give the same B&B: one node per iteration, same
+    bounded-node count and final bounds (node limit reached or converged)"""
+    t = rational_problem(n=2, K=40, n_ineq=1, seed=99)
+    sp = np.array([6, 6], np.int32)
+    ref = oracle.bnb(t, splits=sp, eps_abs=0.0, eps_rel=1e-4, grad_mode="adjoint", tight=True, max_nodes=400)
+    with ivb.Problem(t, grad_mode="adjoint", batched=0) as p:
+        r = p.bnb_solve(t.root_box, splits=sp, batch=1, eps_abs=0.0, eps_rel=1e-4, max_nodes=400)
+    assert (r["nodes"], r["lb"], r["ub"], r["converged"]) == (ref["nodes"], ref["lb"], ref["ub"], ref["converged"])
+
+
+def test_bnb_shifted_squares_closed_form():
+    t = P.shifted_squares(3, [0.3, -1.1, 0.7], [[-2, 2]] * 3)
+    with ivb.Problem(t) as p:
+        r = p.bnb_solve(t.root_box, splits=[8, 8, 8], batch=4, eps_abs=1e-6, eps_rel=0.0, max_nodes=100000)
+    assert r["converged"] and r["lb"] <= 0.0 <= r["ub"] <= 1e-6
+
+
+def test_launch_count_and_tuning_reported():
+    t = rational_problem()
+    boxes, splits = ragged_batch(t, 8, seed=1)
+    with ivb.Problem(t) as p:
+        c0 = p.launch_count()
+        p.bound_nodes(boxes, splits)
+        assert p.launch_count() == c0 + 3
+        tun = p.get_tuning()
+        assert tun["block_threads"] > 0 and tun["blocks_per_sm"] > 0
