@@ -389,7 +389,7 @@ extern "C" ivb_status ivb_create_problem(const ivb_tape* tape, const ivb_options
     CKC(cudaGetDevice(&dev));
     CKC(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev));
     CKC(cudaDeviceGetAttribute(&p->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    for (int m = 0; m < 4; ++m) CKC(set_bound_smem_limit(m, p->smem_optin));
+    for (int m = 0; m < 4; ++m) CKC(set_bound_smem_limit(m, p->smem_optin - 1024));
 
     CKC(cudaMalloc(&p->d_ins, std::max<size_t>(1, ins.size()) * sizeof(Ins)));
     CKC(cudaMalloc(&p->d_rins, std::max<size_t>(1, rins.size()) * sizeof(RIns)));
