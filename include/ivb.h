@@ -210,6 +210,29 @@ ivb_status ivb_bnb_solve(ivb_problem* p, int32_t n, const double* root, const iv
 ivb_status ivb_get_tuning(ivb_problem* p, int32_t* block_threads, int32_t* blocks_per_sm,
                           int32_t* tile, int32_t* frame_in_shared);
 
+/* Static count of the outward-rounded endpoint operations one subdomain
+ * needs under the problem's gradient mode (the canonical formulas: value,
+ * tangent or adjoint rules, Mean Value Form, decode; the kernel computes the
+ * Mean Value Form for every form, so the form does not change it), per category
+ * IVB_CNT_*: the algorithmic work of the bounding kernel per subdomain.
+ * Interval products count two directed multiplies (sign-case selection). */
+enum {
+    IVB_CNT_ADDSUB = 0, IVB_CNT_MUL = 1, IVB_CNT_DIV = 2, IVB_CNT_RCP = 3,
+    IVB_CNT_SQRT = 4, IVB_CNT_EXP = 5, IVB_CNT_LOG = 6, IVB_CNT_RN = 7, IVB_CNT_N = 8
+};
+ivb_status ivb_op_counts(const ivb_problem* p, int64_t counts[IVB_CNT_N]);
+
+/* Throughput of one FP64 primitive on the current GPU in lane operations
+ * per second (a self-timed microbenchmark, 32 warps per SM, 8 independent
+ * chains per thread): IVB_PROBE_DFMA is the FP64 pipe's peak; the directed
+ * add/mul/div/reciprocal/sqrt and exp/log give the cost of each category of
+ * ivb_op_counts in DFMA issue slots. LOG includes one round-to-nearest add. */
+enum {
+    IVB_PROBE_DADD = 0, IVB_PROBE_DMUL = 1, IVB_PROBE_DFMA = 2, IVB_PROBE_DDIV = 3,
+    IVB_PROBE_DRCP = 4, IVB_PROBE_DSQRT = 5, IVB_PROBE_EXP = 6, IVB_PROBE_LOG = 7
+};
+ivb_status ivb_fp64_probe(int32_t which, int32_t iters, double* lane_ops_per_s);
+
 /* Number of kernel launches the library issued on this handle so far. */
 int64_t ivb_launch_count(const ivb_problem* p);
 

@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libivb.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["ivb_kernels.cu", "ivb_api.cu", "ivb_compile.cpp", "ivb_bnb.cpp"]
+SOURCES = ["ivb_kernels.cu", "ivb_api.cu", "ivb_probe.cu", "ivb_compile.cpp", "ivb_bnb.cpp"]
 HEADERS = ["ivb_internal.h", "ivb_iv.cuh", "ivb_kernels.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

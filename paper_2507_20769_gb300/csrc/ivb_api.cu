@@ -693,6 +693,13 @@ extern "C" ivb_status ivb_get_tuning(ivb_problem* p, int32_t* block_threads, int
     return IVB_OK;
 }
 
+extern "C" ivb_status ivb_op_counts(const ivb_problem* p, int64_t counts[IVB_CNT_N]) {
+    if (!p || !counts) return IVB_EINVAL;
+    const int64_t* c = p->opt.grad_mode == IVB_GRAD_ADJOINT ? p->P.cnt_adj : p->P.cnt_fwd;
+    for (int i = 0; i < IVB_CNT_N; ++i) counts[i] = c[i];
+    return IVB_OK;
+}
+
 extern "C" int64_t ivb_launch_count(const ivb_problem* p) { return p ? p->launches : 0; }
 
 extern "C" const char* ivb_last_error(const ivb_problem* p) {

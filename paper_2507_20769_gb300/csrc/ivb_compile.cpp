@@ -250,6 +250,74 @@ std::string compile_tape(const ivb_tape* t, HostProgram& P, std::vector<Ins>& in
         if (units > adj_units_max) adj_units_max = units;
     }
 
+    // ---------------------------------------------------- operation counts
+    // canonical endpoint operations per subdomain (categories of ivb.h)
+    enum { ADD = 0, MUL = 1, DIV = 2, RCP = 3, SQRT = 4, EXP = 5, LOG = 6, RN = 7 };
+    auto value_cost = [](int op, int64_t* c) {
+        switch (op) {
+        case OP_ADD: case OP_SUB: c[ADD] += 2; break;
+        case OP_MUL: case OP_SQR: c[MUL] += 2; break;
+        case OP_DIV: c[DIV] += 2; break;
+        case OP_SQRT: c[SQRT] += 2; break;
+        case OP_EXP: c[EXP] += 2; break;
+        case OP_LOG: c[LOG] += 2; break;
+        }
+    };
+    auto count_values = [&](int32_t begin, int32_t count, int64_t* c) {
+        for (int32_t i = begin; i < begin + count; ++i) value_cost((int)(ins[i].w0 & 31u), c);
+    };
+    auto count_tangents = [&](int32_t begin, int32_t count, int64_t* c) {
+        for (int32_t i = begin; i < begin + count; ++i) {
+            const int op = (int)(ins[i].w0 & 31u);
+            const uint32_t ak = (ins[i].w0 >> 5) & 3u, bk = (ins[i].w0 >> 7) & 3u;
+            const bool az = ak == K_CONST, bz = bk == K_CONST || bk == K_NONE;
+            value_cost(op, c);
+            switch (op) {
+            case OP_ADD: case OP_SUB: if (!az && !bz) c[ADD] += 2LL * n; break;
+            case OP_MUL: if (az || bz) c[MUL] += 2LL * n; else { c[MUL] += 4LL * n; c[ADD] += 2LL * n; } break;
+            case OP_DIV:
+                c[RCP] += 2;
+                if (bz) c[MUL] += 2LL * n;
+                else if (az) c[MUL] += 4LL * n;
+                else { c[MUL] += 4LL * n; c[ADD] += 2LL * n; }
+                break;
+            case OP_SQR: c[MUL] += 2 + 2LL * n; break;
+            case OP_SQRT: c[MUL] += 2 + 2LL * n; c[RCP] += 2; break;
+            case OP_EXP: c[MUL] += 2LL * n; break;
+            case OP_LOG: c[RCP] += 2; c[MUL] += 2LL * n; break;
+            }
+        }
+    };
+    auto count_reverse = [&](int32_t begin, int32_t count, int64_t* c) {
+        for (int32_t i = begin; i < begin + count; ++i) {
+            const RIns& R = rins[i];
+            const int op = (int)(R.w0 & 31u);
+            const bool ai = (R.w0 >> 5) & 1u, bi = (R.w0 >> 6) & 1u, an = (R.w0 >> 7) & 1u, bn = (R.w0 >> 8) & 1u;
+            const int acc = (an ? 0 : (ai ? 0 : 2)) + (bn ? 0 : (bi ? 0 : 2));
+            switch (op) {
+            case OP_VAR: c[ADD] += 2; break;
+            case OP_ADD: case OP_SUB: case OP_NEG: c[ADD] += acc; break;
+            case OP_MUL: c[MUL] += (an ? 0 : 2) + (bn ? 0 : 2); c[ADD] += acc; break;
+            case OP_DIV: c[RCP] += 2; c[MUL] += (an ? 0 : 2) + (bn ? 0 : 4); c[ADD] += acc; break;
+            case OP_SQR: c[MUL] += 4; c[ADD] += acc; break;
+            case OP_SQRT: c[MUL] += 4; c[RCP] += 2; c[ADD] += acc; break;
+            case OP_EXP: c[MUL] += 2; c[ADD] += acc; break;
+            case OP_LOG: c[RCP] += 2; c[MUL] += 2; c[ADD] += acc; break;
+            }
+        }
+    };
+    for (int64_t* c : {P.cnt_fwd, P.cnt_adj}) {
+        c[RN] += 6LL * n;                                   // decode: endpoints and centre
+        count_values(P.pt_begin, P.pt_count, c);            // point sweep f(c)
+        c[ADD] += 4LL * n * no;                             // MVF: X - c and the sum
+        c[MUL] += 2LL * n * no;
+    }
+    count_tangents(P.tan_begin, P.tan_count, P.cnt_fwd);
+    for (int o = 0; o < no; ++o) {
+        count_values(P.adj[o].fw_begin, P.adj[o].fw_count, P.cnt_adj);
+        count_reverse(P.adj[o].rv_begin, P.adj[o].rv_count, P.cnt_adj);
+    }
+
     // ---------------------------------------------------- frame layout
     FrameLayout& L = P.L;
     L.n = n;

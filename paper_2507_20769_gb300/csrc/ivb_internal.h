@@ -91,6 +91,8 @@ struct HostProgram {
     FrameLayout L{};
     // static op counts (per subdomain) for reporting
     int64_t op_hist[16] = {0};
+    // directed endpoint operations per subdomain, per category (ivb.h IVB_CNT_*)
+    int64_t cnt_fwd[8] = {0}, cnt_adj[8] = {0};
 };
 
 }  // namespace ivb

@@ -85,10 +85,12 @@ def lib() -> ctypes.CDLL:
         L.ivb_last_error.argtypes = [P]
         L.ivb_last_error.restype = ctypes.c_char_p
         L.ivb_destroy.argtypes = [P]
+        L.ivb_op_counts.argtypes = [P, P]
+        L.ivb_fp64_probe.argtypes = [I32, I32, P]
         L.ivb_bnb_options_default.argtypes = [P]
         L.ivb_bnb_solve.argtypes = [P, I32, P, P, P, P]
         for f in ("ivb_create_problem", "ivb_bound_nodes", "ivb_bound_nodes_ex", "ivb_enclose", "ivb_point_grad",
-                  "ivb_pick_splits", "ivb_get_tuning", "ivb_bnb_solve"):
+                  "ivb_pick_splits", "ivb_get_tuning", "ivb_bnb_solve", "ivb_op_counts", "ivb_fp64_probe"):
             getattr(L, f).restype = I32
         _lib = L
     return _lib
@@ -171,6 +173,17 @@ def ivb_pick_splits(box, target: int, strategy="adaptive", ref_widths=None) -> n
     s = SPLIT[strategy] if isinstance(strategy, str) else int(strategy)
     _check(lib().ivb_pick_splits(n, _ptr(box), _ptr(ref), int(target), s, _ptr(out)))
     return out
+
+
+CNT_NAMES = ("addsub", "mul", "div", "rcp", "sqrt", "exp", "log", "rn")
+PROBE = {"dadd": 0, "dmul": 1, "dfma": 2, "ddiv": 3, "drcp": 4, "dsqrt": 5, "exp": 6, "log": 7}
+
+
+def ivb_fp64_probe(which: str, iters: int = 512) -> float:
+    """lane operations per second of one FP64 primitive on the current GPU"""
+    v = ctypes.c_double()
+    _check(lib().ivb_fp64_probe(PROBE[which], int(iters), ctypes.byref(v)))
+    return v.value
 
 
 def ivb_last_error(problem=None) -> str:
@@ -295,6 +308,11 @@ class Problem:
         return {"block_threads": v[0].value, "blocks_per_sm": v[1].value, "tile": v[2].value,
                 "frame_in_shared": v[3].value}
 
+    def ivb_op_counts(self) -> dict:
+        c = (ctypes.c_int64 * 8)()
+        _check(lib().ivb_op_counts(self._h, c), self._h)
+        return dict(zip(CNT_NAMES, [int(v) for v in c]))
+
     def ivb_launch_count(self) -> int:
         return int(lib().ivb_launch_count(self._h))
 
@@ -309,3 +327,4 @@ class Problem:
     bnb_solve = ivb_bnb_solve
     get_tuning = ivb_get_tuning
     launch_count = ivb_launch_count
+    op_counts = ivb_op_counts
