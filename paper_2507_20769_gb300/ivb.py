@@ -179,7 +179,7 @@ CNT_NAMES = ("addsub", "mul", "div", "rcp", "sqrt", "exp", "log", "rn")
 PROBE = {"dadd": 0, "dmul": 1, "dfma": 2, "ddiv": 3, "drcp": 4, "dsqrt": 5, "exp": 6, "log": 7}
 
 
-def ivb_fp64_probe(which: str, iters: int = 512) -> float:
+def ivb_fp64_probe(which: str, iters: int = 4096) -> float:
     """lane operations per second of one FP64 primitive on the current GPU"""
     v = ctypes.c_double()
     _check(lib().ivb_fp64_probe(PROBE[which], int(iters), ctypes.byref(v)))
