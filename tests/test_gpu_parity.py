@@ -356,3 +356,28 @@ def test_launch_count_and_tuning_reported():
         assert p.launch_count() == c0 + 3
         tun = p.get_tuning()
         assert tun["block_threads"] > 0 and tun["blocks_per_sm"] > 0
+
+
+# ------------------------------------------------------- autograd Function
+
+def test_autograd_point_grad_against_oracle_and_central_differences():
+    """IvbPointGrad: torch gradients of sum(w * f(x)) equal the oracle's point
+    gradients, and agree with binary128 central differences (h = 1e-6
+    max(1,|x_i|), rel tol 1e-6)"""
+    from paper_2507_20769_gb300.autograd import point_values
+    t = W.config_tape(2)
+    pts = W.sample_points(t.root_box, 16, seed=9)
+    x = torch.tensor(pts, dtype=torch.float64, device=DEV, requires_grad=True)
+    w = torch.linspace(0.5, 2.0, t.n_out, dtype=torch.float64, device=DEV)
+    with ivb.Problem(t) as p:
+        f = point_values(p, x)
+        (f * w).sum().backward()
+    gx = x.grad.cpu().numpy()
+    wn = w.cpu().numpy()
+    for i in range(pts.shape[0]):
+        fo, go = oracle.point_grad(t, pts[i])
+        assert np.allclose(f[i].detach().cpu().numpy(), fo, rtol=1e-12, atol=1e-12)
+        assert np.allclose(gx[i], wn @ go, rtol=1e-10, atol=1e-12)
+        h = 1e-6 * np.maximum(1.0, np.abs(pts[i]))
+        gfd = wn @ oracle.central_diff_q(t, pts[i], h)
+        assert np.all(np.abs(gx[i] - gfd) <= 1e-6 * np.maximum(1.0, np.abs(gx[i])))
