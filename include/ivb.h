@@ -146,6 +146,33 @@ ivb_status ivb_bound_nodes_ex(ivb_problem* p, int32_t n_nodes, const double* box
                               uint8_t* out_infeasible, double* out_ub, double* out_minlo,
                               double* out_maxhi, void* cuda_stream);
 
+/* Allocation-free variant of ivb_bound_nodes (the paper has no counterpart):
+ * for callers that cannot allocate device memory while they run -- e.g. a
+ * service whose GPU memory is reserved up front by another allocator, or a
+ * loop that must not call cudaMalloc/cudaFree because they synchronize the
+ * device and can fail under memory pressure. The call makes no allocation:
+ * the node queue, reduction keys, work counter and an error word live in one
+ * file-scope device array of 512 KiB, per-thread frames in shared memory.
+ *   - boxes, splits_per_dim, out_lb, out_infeasible: DEVICE arrays with the
+ *     layouts of ivb_bound_nodes; 1 <= n_nodes <= IVB_NOALLOC_MAX_NODES
+ *     (larger batches are rejected with IVB_EINVAL); problems whose
+ *     per-thread frame does not fit in shared memory get IVB_ENOTSUP.
+ *   - the first call on a device looks up the array's device address with
+ *     cudaGetSymbolAddress (with that device current); make that first call
+ *     before any stream capture.
+ *   - every call on a device shares the one array and it keeps the last
+ *     call's contents (each call resets what must start fixed: the counter,
+ *     the keys and the error word); calls that overlap on the GPU race with
+ *     each other, so order them (one stream, or events).
+ *   - returns after the work completes: invalid boxes or splits, found on
+ *     the device, are reported as IVB_EINVAL naming the first bad node.
+ *   - the array stays allocated on every GPU that loads the library until
+ *     the process exits. */
+#define IVB_NOALLOC_MAX_NODES 256
+ivb_status ivb_bound_nodes_noalloc(ivb_problem* p, int32_t n_nodes, const double* boxes,
+                                   const int32_t* splits_per_dim, double* out_lb,
+                                   uint8_t* out_infeasible, void* cuda_stream);
+
 /* Per-subdomain enclosures (Step 2 without the reduction) for subdomains
  * first .. first+count-1 of ONE node:
  *   out_F  [count][n_outputs][2]          the enclosure of the chosen form

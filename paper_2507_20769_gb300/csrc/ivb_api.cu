@@ -14,6 +14,7 @@
 #include "../../include/ivb.h"
 #include "ivb_internal.h"
 #include "ivb_kernels.h"
+#include "ivb_problem.h"
 
 namespace ivb {
 std::string validate_tape(const ivb_tape* t);
@@ -23,44 +24,6 @@ std::string compile_tape(const ivb_tape* t, HostProgram& P, std::vector<Ins>& in
 
 using namespace ivb;
 
-struct ivb_problem {
-    ivb_options opt{};
-    HostProgram P{};
-    int n = 0, n_out = 0, obj = 0;
-    uint8_t out_kind[64]{};
-    // program on the device
-    ProgDesc* d_prog = nullptr;
-    Ins* d_ins = nullptr;
-    RIns* d_rins = nullptr;
-    double* d_consts = nullptr;
-    uint8_t* d_out_kind = nullptr;
-    // per-call buffers (capacity max_nodes)
-    int max_nodes = 0;
-    int rec_bytes = 0;
-    char* d_queue = nullptr;
-    char* h_queue = nullptr;            // pinned staging of the queue
-    cudaEvent_t queue_free = nullptr;   // the last copy out of h_queue has completed
-    unsigned long long* d_keys = nullptr;
-    unsigned long long* d_counter = nullptr;
-    double *d_lb = nullptr, *d_ub = nullptr, *d_minlo = nullptr, *d_maxhi = nullptr;
-    uint8_t* d_inf = nullptr;
-    // frames
-    double* d_frame = nullptr;
-    size_t frame_bytes = 0;
-    // tuning
-    int sm_count = 0, smem_optin = 0;
-    bool tuned = false;       // final configuration chosen
-    bool cfg_ready = false;   // some configuration chosen (defaults while waiting for a batch worth tuning on)
-    int block = 128, bps = 4, tile = 512, frame_smem = 0;
-    // graph of the batched call
-    cudaGraphExec_t gexec = nullptr;
-    cudaStream_t cap_stream = nullptr;
-    // point gradients
-    double* d_pframe = nullptr;
-    size_t pframe_bytes = 0;
-    long long launches = 0;
-    std::string err;
-};
 
 namespace {
 

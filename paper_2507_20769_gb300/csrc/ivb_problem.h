@@ -1,0 +1,49 @@
+// ivb_problem.h -- the problem handle behind the opaque ivb_problem of the
+// C ABI, shared by the translation units that implement entry points.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/ivb.h"
+#include "ivb_internal.h"
+#include "ivb_kernels.h"
+
+struct ivb_problem {
+    ivb_options opt{};
+    ivb::HostProgram P{};
+    int n = 0, n_out = 0, obj = 0;
+    uint8_t out_kind[64]{};
+    // program on the device
+    ivb::ProgDesc* d_prog = nullptr;
+    ivb::Ins* d_ins = nullptr;
+    ivb::RIns* d_rins = nullptr;
+    double* d_consts = nullptr;
+    uint8_t* d_out_kind = nullptr;
+    // per-call buffers (capacity max_nodes)
+    int max_nodes = 0;
+    int rec_bytes = 0;
+    char* d_queue = nullptr;
+    char* h_queue = nullptr;            // pinned staging of the queue
+    cudaEvent_t queue_free = nullptr;   // the last copy out of h_queue has completed
+    unsigned long long* d_keys = nullptr;
+    unsigned long long* d_counter = nullptr;
+    double *d_lb = nullptr, *d_ub = nullptr, *d_minlo = nullptr, *d_maxhi = nullptr;
+    uint8_t* d_inf = nullptr;
+    // frames
+    double* d_frame = nullptr;
+    size_t frame_bytes = 0;
+    // tuning
+    int sm_count = 0, smem_optin = 0;
+    bool tuned = false;       // final configuration chosen
+    bool cfg_ready = false;   // some configuration chosen (defaults while waiting for a batch worth tuning on)
+    int block = 128, bps = 4, tile = 512, frame_smem = 0;
+    // graph of the batched call
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    // point gradients
+    double* d_pframe = nullptr;
+    size_t pframe_bytes = 0;
+    long long launches = 0;
+    std::string err;
+};

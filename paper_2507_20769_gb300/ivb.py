@@ -85,12 +85,14 @@ def lib() -> ctypes.CDLL:
         L.ivb_last_error.argtypes = [P]
         L.ivb_last_error.restype = ctypes.c_char_p
         L.ivb_destroy.argtypes = [P]
+        L.ivb_bound_nodes_noalloc.argtypes = [P, I32, P, P, P, P, P]
         L.ivb_op_counts.argtypes = [P, P]
         L.ivb_fp64_probe.argtypes = [I32, I32, P]
         L.ivb_bnb_options_default.argtypes = [P]
         L.ivb_bnb_solve.argtypes = [P, I32, P, P, P, P]
         for f in ("ivb_create_problem", "ivb_bound_nodes", "ivb_bound_nodes_ex", "ivb_enclose", "ivb_point_grad",
-                  "ivb_pick_splits", "ivb_get_tuning", "ivb_bnb_solve", "ivb_op_counts", "ivb_fp64_probe"):
+                  "ivb_pick_splits", "ivb_get_tuning", "ivb_bnb_solve", "ivb_op_counts", "ivb_fp64_probe",
+                  "ivb_bound_nodes_noalloc"):
             getattr(L, f).restype = I32
         _lib = L
     return _lib
@@ -258,6 +260,18 @@ class Problem:
         r = self.ivb_bound_nodes_ex(boxes, splits, want_ub=False, stream=stream)
         return r["lb"], r["infeasible"]
 
+    def ivb_bound_nodes_noalloc(self, boxes, splits, out_lb, out_infeasible, stream=None):
+        """allocation-free bounding for callers that cannot allocate device
+        memory: all four arguments are CUDA tensors (outputs preallocated)"""
+        for x in (boxes, splits, out_lb, out_infeasible):
+            if not (_is_torch(x) and x.is_cuda):
+                raise TypeError("ivb_bound_nodes_noalloc takes CUDA tensors only")
+        nn = int(boxes.shape[0])
+        s = stream if stream is not None else _stream_for(boxes)
+        _check(lib().ivb_bound_nodes_noalloc(self._h, nn, _ptr(boxes), _ptr(splits), _ptr(out_lb),
+                                             _ptr(out_infeasible), s), self._h)
+        return out_lb, out_infeasible
+
     def ivb_enclose(self, box, splits, first=0, count=None, want_fc=False, want_g=False, device=None):
         box = _as(box, np.float64)
         splits = _as(splits, np.int32)
@@ -328,3 +342,4 @@ class Problem:
     get_tuning = ivb_get_tuning
     launch_count = ivb_launch_count
     op_counts = ivb_op_counts
+    bound_nodes_noalloc = ivb_bound_nodes_noalloc
