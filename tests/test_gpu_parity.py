@@ -381,3 +381,52 @@ def test_autograd_point_grad_against_oracle_and_central_differences():
         h = 1e-6 * np.maximum(1.0, np.abs(pts[i]))
         gfd = wn @ oracle.central_diff_q(t, pts[i], h)
         assert np.all(np.abs(gx[i] - gfd) <= 1e-6 * np.maximum(1.0, np.abs(gx[i])))
+
+
+# --------------------------------------------------- other workload configs
+
+def test_config3_uneven_batch_full_size():
+    """configuration 3: 256 nodes of uneven widths (10^U[-4,1] per dim) on the
+    n=6 problem, per-node subdomain targets 2^U{10..20} split by the adaptive
+    picker, one persistent launch. Nodes with <= 2^12 subdomains are checked
+    whole against the oracle; 64 sampled subdomains of large nodes one by one."""
+    t = W.config_tape(3)
+    boxes, targets = W.uneven_nodes(t.n_vars, 256, t.root_box, seed=W.config_seed(3) + 5)
+    ref_w = t.root_box[:, 1] - t.root_box[:, 0]
+    splits = np.stack([ivb.ivb_pick_splits(b, int(tg), "adaptive", ref_w) for b, tg in zip(boxes, targets)])
+    S = np.prod(splits.astype(np.int64), axis=1)
+    with ivb.Problem(t) as p:
+        r = p.bound_nodes_ex(boxes, splits, want_hull=True)
+        small = np.nonzero(S <= 4096)[0][:6]
+        ref = oracle.bound_nodes(t, boxes[small], splits[small], tight=True)
+        hull = np.stack([r["minlo"][small], r["maxhi"][small]], -1)
+        assert_contains_close(hull, np.stack([ref["minlo"], ref["maxhi"]], -1), "config 3 small nodes")
+        big = np.argsort(-S)[:4]
+        rng = np.random.default_rng(3)
+        for nd in big:
+            for k in rng.choice(int(S[nd]), 16, replace=False):
+                F, _, _ = p.enclose(boxes[nd], splits[nd], first=int(k), count=1)
+                Fo, _, _ = oracle.enclose(t, boxes[nd], splits[nd], first=int(k), count=1, tight=True)
+                assert_contains_close(F, Fo, f"config 3 node {nd} subdomain {k}")
+                # the node hull contains every subdomain's enclosure
+                assert np.all(r["minlo"][nd] <= F[0, :, 0]) and np.all(r["maxhi"][nd] >= F[0, :, 1])
+
+
+def test_config5_full_scale_sampled():
+    """configuration 5: n=8, objective + 10 constraints of 1000 entries each,
+    2^24 subdomains in one batched launch (256 nodes x 4^8); sampled
+    subdomains against the oracle one by one, and every sampled enclosure
+    inside its node's hull"""
+    t = W.config_tape(5)
+    boxes = W.bisection_frontier(t.root_box, 256, seed=55)
+    splits = np.full((256, 8), 4, np.int32)
+    with ivb.Problem(t, max_nodes=256) as p:
+        r = p.bound_nodes_ex(boxes, splits, want_hull=True)
+        rng = np.random.default_rng(5)
+        for nd in rng.choice(256, 4, replace=False):
+            for k in rng.choice(65536, 4, replace=False):
+                F, _, _ = p.enclose(boxes[nd], splits[nd], first=int(k), count=1)
+                Fo, _, _ = oracle.enclose(t, boxes[nd], splits[nd], first=int(k), count=1, tight=True)
+                assert_contains_close(F, Fo, f"config 5 node {nd} subdomain {k}")
+                assert np.all(r["minlo"][nd] <= F[0, :, 0]) and np.all(r["maxhi"][nd] >= F[0, :, 1])
+    assert np.all(np.isfinite(r["lb"]))
