@@ -244,23 +244,32 @@ def main():
     d2h = r["lb"].nbytes + r["infeasible"].nbytes + r["ub"].nbytes
 
     # ------------------------------------------------ roofline (FP64 pipe, ALU bound)
-    rates = {k: ivb.ivb_fp64_probe(k) for k in ("dfma", "dadd", "dmul", "ddiv", "drcp", "dsqrt", "exp", "log")}
+    names = ("dfma", "dadd", "dmul", "ddiv", "drcp", "dsqrt", "exp", "log",
+             "own_rcp", "own_div", "own_sqrt", "own_exp", "own_log")
+    rates = {k: ivb.ivb_fp64_probe(k) for k in names}
     peak = rates["dfma"]
-    rates["log"] = 1.0 / max(1.0 / rates["log"] - 1.0 / rates["dadd"], 1e-30)   # probe's log adds one add
-    cost = {"addsub": peak / rates["dadd"], "mul": peak / rates["dmul"], "div": peak / rates["ddiv"],
-            "rcp": peak / rates["drcp"], "sqrt": peak / rates["dsqrt"], "exp": peak / rates["exp"],
-            "log": peak / rates["log"], "rn": peak / rates["dadd"]}
+    for k in ("log", "own_log"):     # both log probes carry one round-to-nearest add
+        rates[k] = 1.0 / max(1.0 / rates[k] - 1.0 / rates["dadd"], 1e-30)
+    # cost of each category in DFMA issue slots: the primitives the kernel runs
+    cost = {"addsub": peak / rates["dadd"], "mul": peak / rates["dmul"], "div": peak / rates["own_div"],
+            "rcp": peak / rates["own_rcp"], "sqrt": peak / rates["own_sqrt"], "exp": peak / rates["own_exp"],
+            "log": peak / rates["own_log"], "rn": peak / rates["dadd"]}
+    vendor = {"addsub": peak / rates["dadd"], "mul": peak / rates["dmul"], "div": peak / rates["ddiv"],
+              "rcp": peak / rates["drcp"], "sqrt": peak / rates["dsqrt"], "exp": peak / rates["exp"],
+              "log": peak / rates["log"], "rn": peak / rates["dadd"]}
     counts = p.op_counts()
     slots_per_sub = sum(counts[k] * cost[k] for k in counts)
+    vendor_slots = sum(counts[k] * vendor[k] for k in counts)
     ops_per_sub = sum(counts.values())
     step_s = t_local / args.steps
     achieved = slots_per_sub * subs_step / step_s
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
-                "unit": "G FP64 DFMA-slot/s", "frac": achieved / peak, "traffic": None,
+                "unit": "G FP64 DFMA-slot/s", "frac": achieved / peak, "traffic": traffic_for(subs_step),
                 "peak_source": "measured live: DFMA lane-op/s of this GPU (ivb_fp64_probe), "
                                f"= {2 * peak / 1e12:.3f} FP64 TFLOP/s",
                 "work_per_subdomain": {"endpoint_ops": ops_per_sub, "dfma_slots": slots_per_sub,
-                                       "counts": counts},
+                                       "counts": counts,
+                                       "dfma_slots_with_cuda_intrinsics": vendor_slots},
                 "primitive_rates_glanes": {k: v / 1e9 for k, v in rates.items()},
                 "kernel_share_note": "step time includes the two tiny key/finalize kernels and the queue copy; "
                                      "the bounding kernel's share is in profiles/"}
@@ -286,6 +295,25 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def traffic_for(subs_step):
+    """DRAM bytes per launch of the bounding kernel from the committed ncu
+    summary, scaled by subdomains, while the kernel source is the one that
+    was profiled; None otherwise"""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_bound_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        rec = json.load(fh)
+    h = hashlib.sha256()
+    for name in ("ivb_kernels.cu", "ivb_iv.cuh", "ivb_fp64x.cuh"):
+        with open(os.path.join(ROOT, "paper_2507_20769_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    if rec.get("kernel_sha256") != h.hexdigest():
+        return None
+    return rec["dram_bytes_per_subdomain"] * subs_step
 
 
 def bnb_compare(t, wl, cap):

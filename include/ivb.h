@@ -203,10 +203,17 @@ ivb_status ivb_pick_splits(int32_t n, const double* box, const double* ref_width
  * measurement harness for time-to-gap. Each iteration pops up to `batch`
  * open nodes of lowest lower bound, bisects each along the dimension of
  * largest width relative to the root box and bounds all children in one
- * ivb_bound_nodes_ex call. Upper bounds are the certified centre-point
- * values of ivb_bound_nodes_ex (no local solver). Nodes are dropped when
- * infeasible or lb >= UB - max(eps_abs, eps_rel |UB|); the run stops when
- * UB - min(open lb) is within that tolerance or a limit is reached. */
+ * ivb_bound_nodes_ex call. Upper bounds (in place of the paper's local
+ * solver): the certified centre-point values of ivb_bound_nodes_ex and, with
+ * corner_ub = 1, a descent-corner point per iteration: for the child with the
+ * smallest centre value, the corner of its box that the sign of the
+ * objective's gradient enclosure over the box points to (centre where the
+ * sign is unknown), else the midpoint between that corner and the centre,
+ * evaluated rigorously and used when certified feasible. All children of an
+ * iteration are bounded and the incumbent updated before any is dropped;
+ * nodes are dropped when infeasible or lb >= UB - max(eps_abs, eps_rel |UB|);
+ * the run stops when UB - min(open lb) is within that tolerance or a limit
+ * is reached. */
 typedef struct {
     int32_t batch;             /* nodes popped per iteration (>= 1)         */
     int32_t split_mode;        /* 0: fixed `splits`; 1 + IVB_SPLIT_*: picker */
@@ -215,6 +222,7 @@ typedef struct {
     double eps_abs, eps_rel;   /* optimality tolerance                      */
     int64_t max_nodes;         /* limit on bounded nodes (0 = none)         */
     double time_limit;         /* seconds (0 = none)                        */
+    int32_t corner_ub;         /* 1: descent-corner upper bounds (default)  */
 } ivb_bnb_options;
 
 typedef struct {
@@ -251,14 +259,27 @@ ivb_status ivb_op_counts(const ivb_problem* p, int64_t counts[IVB_CNT_N]);
 
 /* Throughput of one FP64 primitive on the current GPU in lane operations
  * per second (a self-timed microbenchmark, 32 warps per SM, 8 independent
- * chains per thread): IVB_PROBE_DFMA is the FP64 pipe's peak; the directed
- * add/mul/div/reciprocal/sqrt and exp/log give the cost of each category of
- * ivb_op_counts in DFMA issue slots. LOG includes one round-to-nearest add. */
+ * chains per thread): IVB_PROBE_DFMA is the FP64 pipe's peak; DADD..LOG are
+ * CUDA's directed intrinsics and exp/log; OWN_* are the directed primitives
+ * this library's kernels use (one directed end each, outward widening of
+ * exp/log included) and give the cost of each category of ivb_op_counts in
+ * DFMA issue slots. Both LOG probes include one round-to-nearest add. */
 enum {
     IVB_PROBE_DADD = 0, IVB_PROBE_DMUL = 1, IVB_PROBE_DFMA = 2, IVB_PROBE_DDIV = 3,
-    IVB_PROBE_DRCP = 4, IVB_PROBE_DSQRT = 5, IVB_PROBE_EXP = 6, IVB_PROBE_LOG = 7
+    IVB_PROBE_DRCP = 4, IVB_PROBE_DSQRT = 5, IVB_PROBE_EXP = 6, IVB_PROBE_LOG = 7,
+    IVB_PROBE_OWN_RCP = 8, IVB_PROBE_OWN_DIV = 9, IVB_PROBE_OWN_SQRT = 10,
+    IVB_PROBE_OWN_EXP = 11, IVB_PROBE_OWN_LOG = 12
 };
 ivb_status ivb_fp64_probe(int32_t which, int32_t iters, double* lane_ops_per_s);
+
+/* Test hook: one interval operation of the bounding kernels' own arithmetic
+ * (the natural interval extension of an intrinsic, Section 2.2, with this
+ * library's outward rounding) on n intervals: x, y, r are DEVICE arrays
+ * [n][2]; opcode is a binary or unary tape opcode, or IVB_EVAL_RECIP for the
+ * interval reciprocal 1/x. Enqueued on cuda_stream. */
+#define IVB_EVAL_RECIP 100
+ivb_status ivb_eval_op(int32_t opcode, int64_t n, const double* x, const double* y, double* r,
+                       void* cuda_stream);
 
 /* Number of kernel launches the library issued on this handle so far. */
 int64_t ivb_launch_count(const ivb_problem* p);

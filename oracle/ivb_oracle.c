@@ -742,7 +742,7 @@ void orc_log_enclose(int64_t n, const double* x, int tight, double* lo, double* 
 }
 
 /* One interval operation on arrays of operands (for closed-form op tests):
- * opcode from the tape alphabet, x/y/r as [count][2]. */
+ * opcode from the tape alphabet (100: reciprocal), x/y/r as [count][2]. */
 void orc_iv_op(int opcode, int64_t count, const double* x, const double* y, int tight, double* r) {
     for (int64_t i = 0; i < count; ++i) {
         iv X = {x[2 * i], x[2 * i + 1]}, Y = {0, 0}, R;
@@ -757,6 +757,7 @@ void orc_iv_op(int opcode, int64_t count, const double* x, const double* y, int 
         case OP_EXP: R = iv_exp(X, tight); break;
         case OP_LOG: R = iv_log(X, tight); break;
         case OP_NEG: R = iv_neg(X); break;
+        case 100: R = iv_recip(X); break;   /* interval reciprocal */
         default: R = ENTIRE;
         }
         r[2 * i] = R.lo;
@@ -823,12 +824,18 @@ int orc_pick_splits(int n, const double* box, const double* ref, int64_t target,
  * Best-first spatial B&B (Section 3, Fig. 3) with the oracle's bounding as
  * lower-bounding solver. Each iteration pops the open node of lowest lower
  * bound, bisects it along the dimension of largest width relative to the
- * root box, bounds both children (Steps 1-3), updates the incumbent from
- * the rigorous centre-point upper bounds, and drops children that are
- * infeasible or satisfy lb >= UB - max(eps_abs, eps_rel*|UB|). It stops when
- * UB - min(open lb) <= max(eps_abs, eps_rel*|UB|), the heap is empty, or a
- * node / time limit is reached. Splits per node: the fixed vector `splits`
- * if target <= 0, else orc_pick_splits(target, strategy). */
+ * root box, bounds both children (Steps 1-3), and updates the incumbent from
+ * the children's rigorous centre-point upper bounds and, with corner_ub, from
+ * a descent corner of the child with the smallest centre value: the corner
+ * that the sign of the objective's gradient enclosure over the child's box
+ * points to (centre where the sign is unknown), else the midpoint between
+ * that corner and the centre, used when certified feasible. Only then are
+ * children dropped that are infeasible or satisfy
+ * lb >= UB - max(eps_abs, eps_rel*|UB|). It stops when
+ * UB - min(open lb) <= that tolerance, the heap is empty, or a node / time
+ * limit is reached; the final lower bound is min(open lb, lb of nodes
+ * dropped by the bound test). Splits per node: the fixed vector `splits` if
+ * target <= 0, else orc_pick_splits(target, strategy). */
 typedef struct { double lb; double* box; } bb_node;
 
 static void heap_push(bb_node* h, int64_t* n, bb_node x) {
@@ -862,13 +869,64 @@ static double now_s(void) {
     return ts.tv_sec + 1e-9 * ts.tv_nsec;
 }
 
+/* rigorous objective value at point x, +inf unless certified feasible */
+static double bb_point_value(const tape_t* T, const double* x, int tight) {
+    const int n = T->n_vars;
+    iv* X = malloc((size_t)n * sizeof(iv));
+    iv* V = malloc((size_t)T->n_ops * sizeof(iv));
+    double r = INFINITY;
+    if (X && V) {
+        for (int i = 0; i < n; ++i) { X[i].lo = x[i]; X[i].hi = x[i]; }
+        value_sweep(T, X, V, tight);
+        int feas = 1, obj = 0;
+        for (int q = 0; q < T->n_out; ++q) {
+            const iv v = V[T->out_idx[q]];
+            if (T->out_kind[q] == KIND_OBJ) obj = q;
+            if (T->out_kind[q] == KIND_EQ) feas = 0;
+            if (T->out_kind[q] == KIND_INEQ && !(v.hi <= 0.0)) feas = 0;
+        }
+        if (feas) r = V[T->out_idx[obj]].hi;
+    }
+    free(X); free(V);
+    return r;
+}
+
+/* descent corner of a box (see above) */
+static double bb_corner_value(const tape_t* T, const double* box, int grad_mode, int tight) {
+    const int n = T->n_vars;
+    int obj = 0;
+    for (int q = 0; q < T->n_out; ++q) if (T->out_kind[q] == KIND_OBJ) obj = q;
+    ws_t w;
+    double r = INFINITY;
+    double* cp = malloc((size_t)n * sizeof(double));
+    double* mp = malloc((size_t)n * sizeof(double));
+    if (ws_alloc(&w, T) && cp && mp) {
+        for (int i = 0; i < n; ++i) { w.X[i].lo = box[2 * i]; w.X[i].hi = box[2 * i + 1]; }
+        value_sweep(T, w.X, w.V, tight);
+        const iv* G;
+        if (grad_mode == GRAD_FORWARD) { tangent_sweep(T, w.V, w.D); G = w.D + (size_t)T->out_idx[obj] * n; }
+        else { adjoint_sweep(T, w.V, T->out_idx[obj], w.A, w.G); G = w.G; }
+        for (int i = 0; i < n; ++i) {
+            const double lo = box[2 * i], hi = box[2 * i + 1], c = (lo + hi) * 0.5;
+            cp[i] = G[i].lo > 0.0 ? lo : (G[i].hi < 0.0 ? hi : c);
+            mp[i] = (cp[i] + c) * 0.5;
+        }
+        r = bb_point_value(T, cp, tight);
+        if (!(r < INFINITY)) r = bb_point_value(T, mp, tight);
+    }
+    ws_free(&w);
+    free(cp); free(mp);
+    return r;
+}
+
 /* stats: [0] lb, [1] ub, [2] iterations, [3] nodes bounded, [4] subdomains,
  *        [5] seconds, [6] converged (1/0), [7] open nodes left */
 int orc_bnb(int n_vars, int n_ops, int n_out, const uint8_t* op, const int32_t* a, const int32_t* b,
             const double* c, const int32_t* out_idx, const uint8_t* out_kind, const double* root,
             const int32_t* splits, int64_t target, int strategy, int grad_mode, int form, int tight,
-            double eps_abs, double eps_rel, int64_t max_nodes, double time_limit, double* stats) {
+            double eps_abs, double eps_rel, int64_t max_nodes, double time_limit, int corner_ub, double* stats) {
     const int n = n_vars;
+    tape_t T = make_tape(n_vars, n_ops, n_out, op, a, b, c, out_idx, out_kind);
     int64_t cap = 1024, n_open = 0;
     bb_node* heap = malloc((size_t)cap * sizeof(bb_node));
     double* ref = malloc((size_t)n * sizeof(double));
@@ -878,32 +936,48 @@ int orc_bnb(int n_vars, int n_ops, int n_out, const uint8_t* op, const int32_t* 
     double UB = INFINITY, t0 = now_s();
     int64_t iters = 0, bounded = 0, subs = 0;
     int converged = 0, err = 0;
-    double lb_global = -INFINITY;
-    double lb_pruned = INFINITY;  /* a rigorous global bound also covers nodes dropped by the lb test */
+    double lb_global = -INFINITY, lb_pruned = INFINITY;
+    double* kbox[2];
+    double klb[2], kub[2];
+    uint8_t kinf[2];
 
-    /* bound a box; push it if it survives */
-    #define BOUND_AND_PUSH(BOX)                                                                    \
+    /* bound one box: lb, infeasible flag, centre ub */
+    #define BOUND(BOX, LB, INF, UBV)                                                               \
         do {                                                                                       \
-            double lb_, ub_; uint8_t inf_;                                                        \
             if (target > 0) orc_pick_splits(n, (BOX), ref, target, strategy, sp);                 \
             else memcpy(sp, splits, (size_t)n * sizeof(int32_t));                                 \
             err |= orc_bound_nodes(n, n_ops, n_out, op, a, b, c, out_idx, out_kind, 1, (BOX), sp, \
-                                   grad_mode, form, tight, 0, &lb_, &inf_, &ub_, NULL, NULL);      \
+                                   grad_mode, form, tight, 0, &(LB), &(INF), &(UBV), NULL, NULL);  \
             bounded++; subs += n_subdomains(n, sp);                                               \
-            if (ub_ < UB) UB = ub_;                                                               \
-            double tol_ = fmax(eps_abs, eps_rel * fabs(UB));                                      \
-            if (!inf_ && !(lb_ >= UB - tol_)) {                                                   \
-                if (n_open == cap) { cap *= 2; heap = realloc(heap, (size_t)cap * sizeof(bb_node)); } \
-                heap_push(heap, &n_open, (bb_node){lb_, (BOX)});                                  \
-            } else {                                                                               \
-                if (!inf_ && lb_ < lb_pruned) lb_pruned = lb_;                                    \
-                free(BOX);                                                                         \
+        } while (0)
+    /* incumbent update from a batch of bounded boxes, then push or drop each */
+    #define ABSORB(CNT)                                                                            \
+        do {                                                                                       \
+            int best_ = -1;                                                                        \
+            for (int k_ = 0; k_ < (CNT); ++k_) {                                                   \
+                if (kub[k_] < UB) UB = kub[k_];                                                    \
+                if (best_ < 0 || kub[k_] < kub[best_]) best_ = k_;                                 \
+            }                                                                                      \
+            if (corner_ub && best_ >= 0) {                                                         \
+                double v_ = bb_corner_value(&T, kbox[best_], grad_mode, tight);                   \
+                if (v_ < UB) UB = v_;                                                              \
+            }                                                                                      \
+            for (int k_ = 0; k_ < (CNT); ++k_) {                                                   \
+                double tol_ = fmax(eps_abs, eps_rel * fabs(UB));                                  \
+                if (!kinf[k_] && !(klb[k_] >= UB - tol_)) {                                       \
+                    if (n_open == cap) { cap *= 2; heap = realloc(heap, (size_t)cap * sizeof(bb_node)); } \
+                    heap_push(heap, &n_open, (bb_node){klb[k_], kbox[k_]});                       \
+                } else {                                                                           \
+                    if (!kinf[k_] && klb[k_] < lb_pruned) lb_pruned = klb[k_];                    \
+                    free(kbox[k_]);                                                                \
+                }                                                                                  \
             }                                                                                      \
         } while (0)
 
-    double* rb = malloc((size_t)n * 2 * sizeof(double));
-    memcpy(rb, root, (size_t)n * 2 * sizeof(double));
-    BOUND_AND_PUSH(rb);
+    kbox[0] = malloc((size_t)n * 2 * sizeof(double));
+    memcpy(kbox[0], root, (size_t)n * 2 * sizeof(double));
+    BOUND(kbox[0], klb[0], kinf[0], kub[0]);
+    ABSORB(1);
     while (n_open > 0) {
         const double tol = fmax(eps_abs, eps_rel * fabs(UB));
         lb_global = heap[0].lb;
@@ -920,15 +994,17 @@ int orc_bnb(int n_vars, int n_ops, int n_out, const uint8_t* op, const int32_t* 
         }
         const double lo = nd.box[2 * bi], hi = nd.box[2 * bi + 1];
         const double mid = lo + (hi - lo) * 0.5;
-        double* l = malloc((size_t)n * 2 * sizeof(double));
-        double* r = nd.box;
-        memcpy(l, nd.box, (size_t)n * 2 * sizeof(double));
-        l[2 * bi + 1] = mid;
-        r[2 * bi] = mid;
-        BOUND_AND_PUSH(l);
-        BOUND_AND_PUSH(r);
+        kbox[0] = malloc((size_t)n * 2 * sizeof(double));
+        kbox[1] = nd.box;
+        memcpy(kbox[0], nd.box, (size_t)n * 2 * sizeof(double));
+        kbox[0][2 * bi + 1] = mid;
+        kbox[1][2 * bi] = mid;
+        BOUND(kbox[0], klb[0], kinf[0], kub[0]);
+        BOUND(kbox[1], klb[1], kinf[1], kub[1]);
+        ABSORB(2);
     }
-    #undef BOUND_AND_PUSH
+    #undef BOUND
+    #undef ABSORB
     if (n_open == 0) { converged = 1; lb_global = UB; }
     else lb_global = heap[0].lb;
     if (lb_pruned < lb_global) lb_global = lb_pruned;

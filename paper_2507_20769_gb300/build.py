@@ -17,7 +17,7 @@ LIB = os.path.join(HERE, "libivb.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["ivb_kernels.cu", "ivb_api.cu", "ivb_probe.cu", "ivb_static.cu", "ivb_compile.cpp", "ivb_bnb.cpp"]
-HEADERS = ["ivb_internal.h", "ivb_iv.cuh", "ivb_kernels.h", "ivb_problem.h"]
+HEADERS = ["ivb_internal.h", "ivb_iv.cuh", "ivb_fp64x.cuh", "ivb_kernels.h", "ivb_problem.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC",

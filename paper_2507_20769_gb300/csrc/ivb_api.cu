@@ -197,13 +197,15 @@ struct TuneCand {
 };
 
 // Pick block size, blocks per SM and frame placement by timing the bound
-// kernel on the staged batch (results do not depend on the choice).
+// kernel on the first subdomains of the staged batch (results do not depend on
+// the choice). The timed index range is capped at a few waves of the widest
+// candidate grid so that tuning stays a small fraction of one call.
 ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
     const int mode = kernel_mode(p, false);
-    const int fu = frame_units(p);
     std::vector<TuneCand> cands;
     const int blocks[] = {64, 128, 256};
     const int bpss[] = {1, 2, 4, 8};
+    int max_threads = 0;
     for (int b : blocks)
         for (int k : bpss) {
             const int warps = b * k / 32;
@@ -215,25 +217,33 @@ ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
                 if (p->opt.frame_in_shared == 1 && !sm) continue;
                 if (occupancy_blocks(mode, b, bytes) < k) continue;
                 cands.push_back({b, k, sm});
+                max_threads = std::max(max_threads, b * k * p->sm_count);
             }
         }
     if (cands.empty()) cands.push_back({64, 1, 0});
+    // time only [0, cap) of the global index range
+    const long long cap = std::min<long long>(total, std::max<long long>(4LL * max_threads, 1LL << 18));
+    long long* hdr = reinterpret_cast<long long*>(p->h_queue);
+    const long long g_end = hdr[1];
+    CK(cudaEventSynchronize(p->queue_free));
+    hdr[1] = cap;
+    CK(cudaMemcpyAsync(p->d_queue, p->h_queue, 16, cudaMemcpyHostToDevice, s));
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 1e30f;
     TuneCand bc = cands[0];
+    ivb_status st = IVB_OK;
     for (const TuneCand& c : cands) {
         const int grid = p->sm_count * c.bps;
-        ivb_status st = ensure_frame(p, grid, c.block);
-        if (st) return st;
+        st = ensure_frame(p, grid, c.block);
+        if (st) break;
         const int tile = c.block * 4;
-        // warm-up + timed run on the staged batch
-        for (int rep = 0; rep < 2; ++rep) {
-            if (rep == 1) CK(cudaEventRecord(e0, s));
+        for (int rep = 0; rep < 2 && !st; ++rep) {      // warm-up, then timed
+            if (rep == 1) { cudaError_t ce = cudaEventRecord(e0, s); if (ce) { st = cuda_fail(p, ce, "event"); break; } }
             st = enqueue_bound(p, grid, c.block, tile, c.smem, p->max_nodes, s);
-            if (st) return st;
         }
+        if (st) break;
         CK(cudaEventRecord(e1, s));
         CK(cudaEventSynchronize(e1));
         float ms = 0;
@@ -242,7 +252,11 @@ ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    (void)total;
+    // restore the batch's index range
+    hdr[1] = g_end;
+    CK(cudaMemcpyAsync(p->d_queue, p->h_queue, 16, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    if (st) return st;
     p->block = bc.block;
     p->bps = bc.bps;
     p->frame_smem = bc.smem;
@@ -353,6 +367,7 @@ extern "C" ivb_status ivb_create_problem(const ivb_tape* tape, const ivb_options
     CKC(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev));
     CKC(cudaDeviceGetAttribute(&p->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     for (int m = 0; m < 4; ++m) CKC(set_bound_smem_limit(m, p->smem_optin - 1024));
+    CKC(init_math_tables());
 
     CKC(cudaMalloc(&p->d_ins, std::max<size_t>(1, ins.size()) * sizeof(Ins)));
     CKC(cudaMalloc(&p->d_rins, std::max<size_t>(1, rins.size()) * sizeof(RIns)));
@@ -653,6 +668,21 @@ extern "C" ivb_status ivb_get_tuning(ivb_problem* p, int32_t* block_threads, int
     if (blocks_per_sm) *blocks_per_sm = p->bps;
     if (tile) *tile = p->tile;
     if (frame_in_shared) *frame_in_shared = p->frame_smem;
+    return IVB_OK;
+}
+
+extern "C" ivb_status ivb_eval_op(int32_t opcode, int64_t n, const double* x, const double* y, double* r,
+                                  void* cuda_stream) {
+    if (n < 0 || !x || !r) return fail(nullptr, IVB_EINVAL, "ivb_eval_op: x and r are required");
+    const bool binary = opcode == IVB_OP_ADD || opcode == IVB_OP_SUB || opcode == IVB_OP_MUL || opcode == IVB_OP_DIV;
+    const bool unary = opcode == IVB_OP_SQR || opcode == IVB_OP_SQRT || opcode == IVB_OP_EXP || opcode == IVB_OP_LOG ||
+                       opcode == IVB_OP_NEG || opcode == IVB_EVAL_RECIP;
+    if (!binary && !unary) return fail(nullptr, IVB_EINVAL, "ivb_eval_op: unknown opcode");
+    if (binary && !y) return fail(nullptr, IVB_EINVAL, "ivb_eval_op: binary operation needs y");
+    if (n == 0) return IVB_OK;
+    cudaError_t e = init_math_tables();
+    if (e == cudaSuccess) e = launch_eval_op(opcode, n, x, binary ? y : nullptr, r, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return fail(nullptr, IVB_ECUDA, std::string("ivb_eval_op: ") + cudaGetErrorString(e));
     return IVB_OK;
 }
 

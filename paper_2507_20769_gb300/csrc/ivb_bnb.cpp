@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/ivb.h"
+#include "ivb_problem.h"
 
 namespace {
 
@@ -42,6 +43,7 @@ extern "C" void ivb_bnb_options_default(ivb_bnb_options* o) {
     o->eps_rel = 1e-3;
     o->max_nodes = 0;
     o->time_limit = 0.0;
+    o->corner_ub = 1;
 }
 
 extern "C" ivb_status ivb_bnb_solve(ivb_problem* p, int32_t n, const double* root, const ivb_bnb_options* o,
@@ -80,9 +82,45 @@ extern "C" ivb_status ivb_bnb_solve(ivb_problem* p, int32_t n, const double* roo
         return ivb_bound_nodes_ex(p, cnt, boxes.data(), splits.data(), lb.data(), inf.data(), ub.data(), nullptr,
                                   nullptr, stream);
     };
+    // rigorous value of the objective at a point, +inf unless certified feasible
+    const int n_out = p->n_out, obj = p->obj;
+    std::vector<double> ptbox(2 * n), Fv(2 * n_out), Fcv(2 * n_out), Gv((size_t)2 * n_out * n);
+    std::vector<int32_t> ones(n, 1);
+    auto point_value = [&](const double* x) -> double {
+        for (int i = 0; i < n; ++i) { ptbox[2 * i] = x[i]; ptbox[2 * i + 1] = x[i]; }
+        if (ivb_enclose(p, ptbox.data(), ones.data(), 0, 1, Fv.data(), Fcv.data(), nullptr, stream) != IVB_OK)
+            return INFINITY;
+        if (p->P.has_eq) return INFINITY;
+        for (int q = 0; q < n_out; ++q)
+            if (p->out_kind[q] == IVB_OUT_INEQ && !(Fcv[2 * q + 1] <= 0.0)) return INFINITY;
+        return Fcv[2 * obj + 1];
+    };
+    // descent corner of a box: the sign of the objective's gradient enclosure
+    // over the box picks lo or hi per dimension, the centre where it is unknown
+    std::vector<double> cpt(n), mpt(n);
+    auto corner_value = [&](const double* box) -> double {
+        if (ivb_enclose(p, box, ones.data(), 0, 1, Fv.data(), nullptr, Gv.data(), stream) != IVB_OK) return INFINITY;
+        const double* G = Gv.data() + (size_t)obj * n * 2;
+        for (int i = 0; i < n; ++i) {
+            const double lo = box[2 * i], hi = box[2 * i + 1], c = (lo + hi) * 0.5;
+            cpt[i] = G[2 * i] > 0.0 ? lo : (G[2 * i + 1] < 0.0 ? hi : c);
+            mpt[i] = (cpt[i] + c) * 0.5;
+        }
+        const double v = point_value(cpt.data());
+        if (v < INFINITY) return v;
+        return point_value(mpt.data());
+    };
     auto absorb = [&](int cnt) {
+        int best = -1;
         for (int k = 0; k < cnt; ++k) {
             if (ub[k] < UB) UB = ub[k];
+            if (best < 0 || ub[k] < ub[best]) best = k;
+        }
+        if (o->corner_ub && best >= 0) {
+            const double v = corner_value(kids[best]->box.data());
+            if (v < UB) UB = v;
+        }
+        for (int k = 0; k < cnt; ++k) {
             const double tol = std::max(o->eps_abs, o->eps_rel * std::fabs(UB));
             if (!inf[k] && !(lb[k] >= UB - tol)) {
                 kids[k]->lb = lb[k];

@@ -1,0 +1,229 @@
+// ivb_fp64x.cuh -- directed-rounding FP64 primitives built for a narrow FP64
+// pipe (GB300: one FP64 warp instruction per 64 cycles per SM sub-partition,
+// integer / FP32 / MUFU pipes many times wider).
+//
+// Division, reciprocal, square root (Markstein's method, IBM J. Res. Dev. 34,
+// 1990: Newton-Raphson with fused multiply-add and a final remainder): a
+// 23-bit seed from the FP32 MUFU approximations (rcp.approx / rsqrt.approx) of
+// a float assembled from the double's bits on the integer pipe, FP64 Newton
+// steps, then the sign of an exact FMA remainder decides which neighbour is
+// the correctly rounded result toward -inf or +inf. The results are the
+// correctly rounded directed values (identical to __ddiv_rd & co.); inputs
+// outside the fast path's exponent range, and results that are powers of two
+// (where the spacing of doubles changes), take the CUDA intrinsic.
+//
+// exp and log (Tang's table-driven method, ACM TOMS 15(2) 1989 and 16(4)
+// 1990): exp(x) = 2^m 2^(j/128) e^r with |r| <= ln2/256 and a degree-5
+// polynomial; log(x) = m ln2 - log(c_j) + log1p(x 2^-m c_j - 1) with 256
+// reciprocal centres c_j and a degree-7 polynomial. Tables are double-double,
+// computed on the host in extended precision. Error before widening below 1.5
+// ulp of the result; the interval ends are then moved two neighbour steps
+// outward, which encloses the true value.
+#pragma once
+#include <cstdint>
+
+namespace ivb {
+
+// tables, in device memory of this module (filled by init_math_tables)
+struct MathTables {
+    double exp_hi[128], exp_lo[128];   // 2^(j/128) as hi + lo
+    double log_c[256];                 // reciprocal centres c_j
+    double log_hi[256], log_lo[256];   // -log(c_j) as hi + lo
+};
+static __device__ MathTables g_math;
+
+__device__ __forceinline__ float rcp_approx_f(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_approx_f(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ int bexp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
+__device__ __forceinline__ bool mant_zero(double x) { return (__double_as_longlong(x) & 0x000FFFFFFFFFFFFFLL) == 0; }
+__device__ __forceinline__ double up1(double y) {   // next toward +inf, y finite nonzero
+    long long b = __double_as_longlong(y);
+    return __longlong_as_double(b >= 0 ? b + 1 : b - 1);
+}
+__device__ __forceinline__ double dn1(double y) {   // next toward -inf, y finite nonzero
+    long long b = __double_as_longlong(y);
+    return __longlong_as_double(b >= 0 ? b - 1 : b + 1);
+}
+__device__ __forceinline__ bool sgn_ge0(double x) { long long b = __double_as_longlong(x); return b >= 0 || b == (long long)0x8000000000000000ULL; }
+__device__ __forceinline__ bool sgn_le0(double x) { return __double_as_longlong(x) <= 0 || __double_as_longlong(x) == (long long)0x8000000000000000ULL; }
+
+// 1/y seed for y > 0 with biased exponent E in [1, 2044]: relative error < 2^-21
+__device__ __forceinline__ double rcp_seed(double y) {
+    const long long b = __double_as_longlong(y);
+    const int E = (int)((b >> 52) & 0x7FF);
+    const float m = __int_as_float(0x3F800000 | (int)((b >> 29) & 0x7FFFFF));   // y's mantissa in [1,2)
+    const int rb = __float_as_int(rcp_approx_f(m));                              // (0.5, 1]
+    const int fe = (rb >> 23) & 0xFF;
+    const long long db = ((long long)(fe - 127 + 2046 - E) << 52) | ((long long)(rb & 0x7FFFFF) << 29);
+    return __longlong_as_double(db);
+}
+
+// fast-path exponent window: products, quotients and remainders stay normal
+__device__ __forceinline__ bool safe_e(int E) { return E >= 64 && E <= 1980; }
+
+// ---------------------------------------------------------------- reciprocal
+// correctly rounded 1/y toward -inf (up = false) or +inf (up = true), y > 0
+__device__ __forceinline__ double rcp_dir_pos(double y, bool up) {
+    if (safe_e(bexp(y))) {
+        double r = rcp_seed(y);
+        double e = __fma_rn(-y, r, 1.0);
+        r = __fma_rn(r, e, r);
+        e = __fma_rn(-y, r, 1.0);
+        r = __fma_rn(r, e, r);                       // within 0.5 ulp + 2^-80 relative
+        if (!mant_zero(r)) {
+            const double rho = __fma_rn(-y, r, 1.0);  // sign(1/y - r)
+            if (up) return (sgn_le0(rho)) ? r : up1(r);
+            return (sgn_ge0(rho)) ? r : dn1(r);
+        }
+    }
+    return up ? __drcp_ru(y) : __drcp_rd(y);
+}
+
+// ---------------------------------------------------------------- division
+// seed-refined reciprocal of y > 0 (relative error < 2^-42), or 0 when y is
+// outside the fast path
+__device__ __forceinline__ double rcp_refined(double y) {
+    if (!safe_e(bexp(y))) return 0.0;
+    const double r = rcp_seed(y);
+    return __fma_rn(r, __fma_rn(-y, r, 1.0), r);
+}
+
+// correctly rounded x/y toward -inf or +inf, y > 0, given r = rcp_refined(y)
+__device__ __forceinline__ double div_dir_pos(double x, double y, double r, bool up) {
+    const int Ex = bexp(x), Ey = bexp(y);
+    const bool x0 = (__double_as_longlong(x) << 1) == 0;
+    if (__double_as_longlong(r) != 0 && (x0 || (safe_e(Ex) && Ex - Ey <= 900 && Ey - Ex <= 900))) {
+        if (x0) return x * r;                          // exact +-0
+        const double q0 = x * r;
+        const double q = __fma_rn(__fma_rn(-y, q0, x), r, q0);   // within 0.5 ulp + 2^-80 relative
+        if (!mant_zero(q)) {
+            const double rho = __fma_rn(-y, q, x);     // sign(x/y - q)
+            if (up) return sgn_le0(rho) ? q : up1(q);
+            return sgn_ge0(rho) ? q : dn1(q);
+        }
+    }
+    return up ? __ddiv_ru(x, y) : __ddiv_rd(x, y);
+}
+
+// directed reciprocal for y of either sign (y != 0, finite or infinite)
+__device__ __forceinline__ double rcp_dn(double y) {
+    return __double_as_longlong(y) > 0 ? rcp_dir_pos(y, false) : -rcp_dir_pos(-y, true);
+}
+__device__ __forceinline__ double rcp_up(double y) {
+    return __double_as_longlong(y) > 0 ? rcp_dir_pos(y, true) : -rcp_dir_pos(-y, false);
+}
+
+// ---------------------------------------------------------------- square root
+// correctly rounded sqrt(x) toward -inf or +inf, x >= 0
+__device__ __forceinline__ double sqrt_dir(double x, bool up) {
+    const long long b = __double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7FF);
+    if (safe_e(E)) {
+        // x = m 2^e, e = E - 1023; seed for 1/sqrt of m' = m or 2m so that the exponent halves
+        const int odd = (E + 1) & 1;                 // e odd
+        const float mf = __int_as_float(((127 + odd) << 23) | (int)((b >> 29) & 0x7FFFFF));   // [1,4)
+        const int rb = __float_as_int(rsqrt_approx_f(mf));
+        const int fe = (rb >> 23) & 0xFF;
+        const int h = (E - 1023 - odd) / 2;          // exact: E - 1023 - odd is even
+        const double r0 = __longlong_as_double(((long long)(fe - 127 - h + 1023) << 52) | ((long long)(rb & 0x7FFFFF) << 29));
+        double g = x * r0;                           // ~sqrt(x)
+        double hh = __longlong_as_double(__double_as_longlong(r0) - (1LL << 52));   // r0 / 2, exact
+        const double eps = __fma_rn(-g, hh, 0.5);
+        g = __fma_rn(g, eps, g);
+        hh = __fma_rn(hh, eps, hh);
+        g = __fma_rn(__fma_rn(-g, g, x), hh, g);     // within 0.5 ulp + tiny
+        if (!mant_zero(g)) {
+            const double d = __fma_rn(-g, g, x);     // sign(sqrt(x) - g)
+            if (up) return sgn_le0(d) ? g : up1(g);
+            return sgn_ge0(d) ? g : dn1(g);
+        }
+    }
+    return up ? __dsqrt_ru(x) : __dsqrt_rd(x);
+}
+
+// ---------------------------------------------------------------- exp
+// double whose value is the integer k (|k| < 2^31), one FP64 add
+__device__ __forceinline__ double int_to_double(int k) {
+    return __longlong_as_double(0x4338000000000000LL + (long long)k) - 6755399441055744.0;
+}
+
+// exp(x) for |x| <= 700 (fast path): one final rounding plus < 2^-59 relative
+__device__ __forceinline__ double exp_core(double x, bool* ok) {
+    const long long b = __double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7FF);
+    if ((b & 0x7FFFFFFFFFFFFFFFLL) > 0x4085E00000000000LL) { *ok = false; return 0.0; }   // |x| > 700
+    *ok = true;
+    // k = round(x 128/ln2), from a float copy of x (any k within one of the rounded value works)
+    float xf = 0.0f;
+    if (E >= 1023 - 100) xf = __int_as_float((int)((b >> 32) & 0x80000000) | ((E - 1023 + 127) << 23) | (int)((b >> 29) & 0x7FFFFF));
+    const int k = __float2int_rn(xf * 184.66496523378731f);
+    const double kd = int_to_double(k);
+    // r = x - k ln2/128 with ln2/128 = C1 + C2: C1 is ln2/128 rounded to 33 significant
+    // bits (k C1 is exact for |k| < 2^17), C2 the remainder rounded to nearest
+    const double C1 = 0x1.62e42ff000000p-8, C2 = -0x1.718432a1b0e26p-42;
+    double r = __fma_rn(-kd, C1, x);
+    r = __fma_rn(-kd, C2, r);
+    // p = e^r - 1, |r| < 0.0028: truncation below 2^-60
+    double u = __fma_rn(r, 1.0 / 120.0, 1.0 / 24.0);
+    u = __fma_rn(r, u, 1.0 / 6.0);
+    u = __fma_rn(r, u, 0.5);
+    u = __fma_rn(r, u, 1.0);
+    const double p = r * u;
+    const int j = k & 127, m = k >> 7;
+    const double th = g_math.exp_hi[j], tl = g_math.exp_lo[j];
+    const double y = th + __fma_rn(th, p, tl);       // 2^(j/128) (1 + p), one final rounding
+    return __longlong_as_double(__double_as_longlong(y) + ((long long)m << 52));
+}
+
+// log(x) for normal x > 0 (fast path), error below 1.5 ulp of the result
+__device__ __forceinline__ double log_core(double x, bool* ok) {
+    const long long b = __double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7FF);
+    if (b <= 0 || E == 0 || E == 0x7FF) { *ok = false; return 0.0; }
+    *ok = true;
+    int m = E - 1023;
+    const long long mant = b & 0x000FFFFFFFFFFFFFLL;
+    const int j = (int)(mant >> 44);                 // top 8 mantissa bits
+    long long yb = 0x3FF0000000000000LL | mant;       // y in [1, 2)
+    if (j >= 128) { yb -= (1LL << 52); m += 1; }      // y in [0.75, 1)
+    const double y = __longlong_as_double(yb);
+    const double r = __fma_rn(y, g_math.log_c[j], -1.0);   // |r| <= 2^-8
+    // log1p(r) = r + r^2 P(r), P to degree 5: truncation below 2^-66
+    double P = __fma_rn(r, 1.0 / 7.0, -1.0 / 6.0);
+    P = __fma_rn(r, P, 1.0 / 5.0);
+    P = __fma_rn(r, P, -0.25);
+    P = __fma_rn(r, P, 1.0 / 3.0);
+    P = __fma_rn(r, P, -0.5);
+    const double md = int_to_double(m);
+    // ln2 = LN2_HI + LN2_LO: LN2_HI is ln2 rounded to 42 significant bits (m LN2_HI is
+    // exact for |m| < 2^11), LN2_LO the remainder rounded to nearest
+    const double LN2_HI = 0x1.62e42fefa3800p-1, LN2_LO = 0x1.ef35793c76730p-45;
+    const double hi = __fma_rn(md, LN2_HI, g_math.log_hi[j]);
+    const double lo = __fma_rn(md, LN2_LO, g_math.log_lo[j]);
+    const double s = __fma_rn(r * r, P, r) + lo;
+    return hi + s;
+}
+
+__device__ __forceinline__ double exp_dir(double x, bool up) {
+    bool ok;
+    double y = exp_core(x, &ok);
+    if (!ok) y = exp(x);
+    return up ? next_up(next_up(y)) : next_dn(next_dn(y));
+}
+__device__ __forceinline__ double log_dir(double x, bool up) {   // x > 0
+    bool ok;
+    double y = log_core(x, &ok);
+    if (!ok) y = log(x);
+    return up ? next_up(next_up(y)) : next_dn(next_dn(y));
+}
+
+}  // namespace ivb

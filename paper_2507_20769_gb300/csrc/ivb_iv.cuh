@@ -61,6 +61,12 @@ __device__ __forceinline__ double next_up(double y) {
 }
 __device__ __forceinline__ double next_dn(double y) { return ineg(next_up(ineg(y))); }
 
+}  // namespace ivb
+
+#include "ivb_fp64x.cuh"
+
+namespace ivb {
+
 // ---------------------------------------------------------------- endpoints
 __device__ __forceinline__ double add_dn(double x, double y) { return __dadd_rd(x, y); }
 __device__ __forceinline__ double add_up(double x, double y) { return __dadd_ru(x, y); }
@@ -123,7 +129,7 @@ __device__ __forceinline__ iv iv_sqr(iv x) {
 // reciprocal of an interval without 0 (ENTIRE otherwise)
 __device__ __forceinline__ iv iv_recip(iv y) {
     if (!(gt0(y.lo) || lt0(y.hi))) return entire();
-    return mk(__drcp_rd(y.hi), __drcp_ru(y.lo));
+    return mk(rcp_dn(y.hi), rcp_up(y.lo));
 }
 __device__ __forceinline__ iv iv_recip_pos(iv y) { return gt0(y.lo) ? iv_recip(y) : entire(); }
 
@@ -136,24 +142,25 @@ __device__ __forceinline__ iv iv_div(iv x, iv y) {
     if (yneg) { xl = ineg(x.hi); xh = ineg(x.lo); yl = ineg(y.hi); yh = ineg(y.lo); }
     const double dl = ge0(xl) ? yh : yl;
     const double dh = ge0(xh) ? yl : yh;
-    return mk(__ddiv_rd(xl, dl), __ddiv_ru(xh, dh));
+    const double rl = rcp_refined(dl);
+    const double rh = (bits(dh) == bits(dl)) ? rl : rcp_refined(dh);
+    return mk(div_dir_pos(xl, dl, rl, false), div_dir_pos(xh, dh, rh, true));
 }
 
 __device__ __forceinline__ iv iv_sqrt(iv x) {
     if (lt0(x.lo)) return entire();
-    return mk(__dsqrt_rd(x.lo), __dsqrt_ru(x.hi));
+    return mk(sqrt_dir(x.lo, false), sqrt_dir(x.hi, true));
 }
 
-// exp / log: CUDA's double exp and log are within one ulp; two neighbour
-// steps outward enclose the true value also where the spacing of doubles
-// changes between the result and the true value (binade boundaries).
+// exp / log: table-driven evaluation (ivb_fp64x.cuh) widened two neighbour
+// steps outward; the lower end of exp is clamped at 0.
 __device__ __forceinline__ double exp_dn(double x) {
-    double r = next_dn(next_dn(exp(x)));
+    double r = exp_dir(x, false);
     return lt0(r) ? 0.0 : r;
 }
-__device__ __forceinline__ double exp_up(double x) { return next_up(next_up(exp(x))); }
-__device__ __forceinline__ double log_dn(double x) { return next_dn(next_dn(log(x))); }
-__device__ __forceinline__ double log_up(double x) { return next_up(next_up(log(x))); }
+__device__ __forceinline__ double exp_up(double x) { return exp_dir(x, true); }
+__device__ __forceinline__ double log_dn(double x) { return log_dir(x, false); }
+__device__ __forceinline__ double log_up(double x) { return log_dir(x, true); }
 
 __device__ __forceinline__ iv iv_exp(iv x) { return mk(exp_dn(x.lo), exp_up(x.hi)); }
 __device__ __forceinline__ iv iv_log(iv x) {

@@ -9,7 +9,9 @@
 // One persistent kernel serves any number of nodes: blocks grab tiles of the
 // global subdomain index space from a device counter and map indices to nodes
 // through the node queue's prefix sums.
+#include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "ivb_internal.h"
 #include "ivb_iv.cuh"
@@ -563,6 +565,109 @@ __global__ void __launch_bounds__(256) k_point_grad(const ProgDesc* __restrict__
             for (int i = 0; i < n; ++i) grad[((size_t)p * n_out + o) * n + i] = F.ld(gb + i);
         }
     }
+}
+
+// ------------------------------------------------------------ test hook
+// opcode: tape opcodes of the interval operations, or 100 for the reciprocal
+__global__ void k_eval_op(int opcode, long long n, const double* __restrict__ x, const double* __restrict__ y,
+                          double* r) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const iv X = mk(x[2 * i], x[2 * i + 1]);
+        const iv Y = y ? mk(y[2 * i], y[2 * i + 1]) : X;
+        const iv R = opcode == 100 ? iv_recip(X) : eval_value((uint32_t)opcode, X, Y);
+        r[2 * i] = R.lo;
+        r[2 * i + 1] = R.hi;
+    }
+}
+
+cudaError_t launch_eval_op(int opcode, long long n, const double* x, const double* y, double* r, cudaStream_t s) {
+    const int block = 256;
+    const long long g = (n + block - 1) / block;
+    k_eval_op<<<(int)(g < 4096 ? g : 4096), block, 0, s>>>(opcode, n, x, y, r);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ own-primitive probe
+// throughput of this library's directed primitives (ivb_fp64x.cuh), the
+// same shape as ivb_probe.cu: 8 independent chains per thread
+template <int W>
+__global__ void k_own_probe(double* out, double seed, int iters) {
+    double x[8];
+    const double y = seed + threadIdx.x * 1e-12;
+    for (int j = 0; j < 8; ++j) x[j] = 1.5 + j * 1e-3 + threadIdx.x * 1e-9;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (W == 0) x[j] = rcp_dir_pos(x[j], false);
+            if (W == 1) x[j] = div_dir_pos(y, x[j], rcp_refined(x[j]), false);
+            if (W == 2) x[j] = sqrt_dir(x[j], false);
+            if (W == 3) x[j] = exp_dir(-x[j], false);
+            if (W == 4) x[j] = __dadd_rn(log_dir(x[j], false), 2.0);
+        }
+    }
+    double acc = 0.0;
+    for (int j = 0; j < 8; ++j) acc += x[j];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+template <int W>
+static cudaError_t own_probe_run(double* out, int grid, int block, int iters, float* ms) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    k_own_probe<W><<<grid, block>>>(out, 1.0000001, iters / 4 + 1);
+    cudaEventRecord(a);
+    k_own_probe<W><<<grid, block>>>(out, 1.0000001, iters);
+    cudaEventRecord(b);
+    cudaError_t e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e;
+}
+
+cudaError_t run_own_probe(int which, double* out, int grid, int block, int iters, float* ms) {
+    cudaError_t e = init_math_tables();
+    if (e != cudaSuccess) return e;
+    switch (which) {
+    case 0: return own_probe_run<0>(out, grid, block, iters, ms);
+    case 1: return own_probe_run<1>(out, grid, block, iters, ms);
+    case 2: return own_probe_run<2>(out, grid, block, iters, ms);
+    case 3: return own_probe_run<3>(out, grid, block, iters, ms);
+    default: return own_probe_run<4>(out, grid, block, iters, ms);
+    }
+}
+
+// exp/log tables in extended precision on the host (long double: 64-bit
+// significand on x86-64, binary128 on AArch64), split into double hi + lo
+cudaError_t init_math_tables() {
+    static bool done[256] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 256 && done[dev]) return cudaSuccess;
+    MathTables h;
+    for (int j = 0; j < 128; ++j) {
+        const long double v = exp2l((long double)j / 128.0L);
+        h.exp_hi[j] = (double)v;
+        h.exp_lo[j] = (double)(v - (long double)h.exp_hi[j]);
+    }
+    for (int j = 0; j < 256; ++j) {
+        // y in [1 + j/256, 1 + (j+1)/256); j >= 128 is folded to y/2 in [0.75, 1)
+        double c = 1.0;
+        if (j != 0 && j != 255) {
+            const long double F = (j < 128) ? 1.0L + (j + 0.5L) / 256.0L : (1.0L + (j + 0.5L) / 256.0L) / 2.0L;
+            c = (double)(1.0L / F);
+        }
+        const long double L = -logl((long double)c);
+        h.log_c[j] = c;
+        h.log_hi[j] = (double)L;
+        h.log_lo[j] = (double)(L - (long double)h.log_hi[j]);
+    }
+    e = cudaMemcpyToSymbol(g_math, &h, sizeof(h));
+    if (e == cudaSuccess && dev >= 0 && dev < 256) done[dev] = true;
+    return e;
 }
 
 // ------------------------------------------------------------ host wrappers

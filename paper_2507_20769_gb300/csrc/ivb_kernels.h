@@ -78,5 +78,12 @@ cudaError_t launch_point_grad(const ProgDesc* prog, int n, int n_out, int frame_
                               const double* x, double* f, double* grad, double* gframe, int grid, int block,
                               cudaStream_t s);
 int occupancy_blocks(int mode, int block, size_t smem);
+// fill the exp/log tables of the current device (once per device)
+cudaError_t init_math_tables();
+// throughput run of one of this library's directed primitives (0 rcp, 1 div,
+// 2 sqrt, 3 exp, 4 log) for ivb_fp64_probe
+cudaError_t run_own_probe(int which, double* out, int grid, int block, int iters, float* ms);
+// one interval operation of the kernels' arithmetic on arrays (test hook)
+cudaError_t launch_eval_op(int opcode, long long n, const double* x, const double* y, double* r, cudaStream_t s);
 
 }  // namespace ivb

@@ -7,6 +7,7 @@
 #include <cstdint>
 
 #include "../../include/ivb.h"
+#include "ivb_kernels.h"
 
 namespace {
 
@@ -58,7 +59,7 @@ cudaError_t run(double* out, int grid, int block, int iters, float* ms) {
 }  // namespace
 
 extern "C" ivb_status ivb_fp64_probe(int32_t which, int32_t iters, double* lane_ops_per_s) {
-    if (!lane_ops_per_s || iters < 1 || which < 0 || which > IVB_PROBE_LOG) return IVB_EINVAL;
+    if (!lane_ops_per_s || iters < 1 || which < 0 || which > IVB_PROBE_OWN_LOG) return IVB_EINVAL;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return IVB_ECUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return IVB_ECUDA;
@@ -68,6 +69,10 @@ extern "C" ivb_status ivb_fp64_probe(int32_t which, int32_t iters, double* lane_
     float ms = 0.f;
     cudaError_t e;
     switch (which) {
+    case IVB_PROBE_OWN_RCP: case IVB_PROBE_OWN_DIV: case IVB_PROBE_OWN_SQRT: case IVB_PROBE_OWN_EXP:
+    case IVB_PROBE_OWN_LOG:
+        e = ivb::run_own_probe(which - IVB_PROBE_OWN_RCP, out, grid, block, iters, &ms);
+        break;
     case IVB_PROBE_DADD: e = run<IVB_PROBE_DADD>(out, grid, block, iters, &ms); break;
     case IVB_PROBE_DMUL: e = run<IVB_PROBE_DMUL>(out, grid, block, iters, &ms); break;
     case IVB_PROBE_DFMA: e = run<IVB_PROBE_DFMA>(out, grid, block, iters, &ms); break;

@@ -46,7 +46,7 @@ class ivb_tape(ctypes.Structure):
 class ivb_bnb_options(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int32), ("split_mode", ctypes.c_int32), ("splits", ctypes.c_void_p),
                 ("target", ctypes.c_int64), ("eps_abs", ctypes.c_double), ("eps_rel", ctypes.c_double),
-                ("max_nodes", ctypes.c_int64), ("time_limit", ctypes.c_double)]
+                ("max_nodes", ctypes.c_int64), ("time_limit", ctypes.c_double), ("corner_ub", ctypes.c_int32)]
 
 
 class ivb_bnb_result(ctypes.Structure):
@@ -86,13 +86,14 @@ def lib() -> ctypes.CDLL:
         L.ivb_last_error.restype = ctypes.c_char_p
         L.ivb_destroy.argtypes = [P]
         L.ivb_bound_nodes_noalloc.argtypes = [P, I32, P, P, P, P, P]
+        L.ivb_eval_op.argtypes = [I32, I64, P, P, P, P]
         L.ivb_op_counts.argtypes = [P, P]
         L.ivb_fp64_probe.argtypes = [I32, I32, P]
         L.ivb_bnb_options_default.argtypes = [P]
         L.ivb_bnb_solve.argtypes = [P, I32, P, P, P, P]
         for f in ("ivb_create_problem", "ivb_bound_nodes", "ivb_bound_nodes_ex", "ivb_enclose", "ivb_point_grad",
                   "ivb_pick_splits", "ivb_get_tuning", "ivb_bnb_solve", "ivb_op_counts", "ivb_fp64_probe",
-                  "ivb_bound_nodes_noalloc"):
+                  "ivb_bound_nodes_noalloc", "ivb_eval_op"):
             getattr(L, f).restype = I32
         _lib = L
     return _lib
@@ -178,14 +179,31 @@ def ivb_pick_splits(box, target: int, strategy="adaptive", ref_widths=None) -> n
 
 
 CNT_NAMES = ("addsub", "mul", "div", "rcp", "sqrt", "exp", "log", "rn")
-PROBE = {"dadd": 0, "dmul": 1, "dfma": 2, "ddiv": 3, "drcp": 4, "dsqrt": 5, "exp": 6, "log": 7}
+PROBE = {"dadd": 0, "dmul": 1, "dfma": 2, "ddiv": 3, "drcp": 4, "dsqrt": 5, "exp": 6, "log": 7,
+         "own_rcp": 8, "own_div": 9, "own_sqrt": 10, "own_exp": 11, "own_log": 12}
 
 
-def ivb_fp64_probe(which: str, iters: int = 4096) -> float:
+def ivb_fp64_probe(which: str, iters: int = 1024) -> float:
     """lane operations per second of one FP64 primitive on the current GPU"""
     v = ctypes.c_double()
     _check(lib().ivb_fp64_probe(PROBE[which], int(iters), ctypes.byref(v)))
     return v.value
+
+
+IVB_EVAL_RECIP = 100
+
+
+def ivb_eval_op(opcode: int, x, y=None):
+    """test hook: one interval operation of the kernels' arithmetic on CUDA
+    tensors of intervals [n, 2]; returns a new [n, 2] tensor"""
+    import torch
+    if not (_is_torch(x) and x.is_cuda):
+        raise TypeError("ivb_eval_op takes CUDA tensors")
+    x = x.contiguous()
+    y = None if y is None else y.contiguous()
+    r = torch.empty_like(x)
+    _check(lib().ivb_eval_op(int(opcode), int(x.shape[0]), _ptr(x), _ptr(y), _ptr(r), _stream_for(x)))
+    return r
 
 
 def ivb_last_error(problem=None) -> str:
@@ -296,7 +314,7 @@ class Problem:
         return f, g
 
     def ivb_bnb_solve(self, root, splits=None, target=0, strategy="adaptive", batch=1, eps_abs=0.0,
-                      eps_rel=1e-3, max_nodes=0, time_limit=0.0):
+                      eps_rel=1e-3, max_nodes=0, time_limit=0.0, corner_ub=1):
         root = np.ascontiguousarray(root, dtype=np.float64)
         o = ivb_bnb_options()
         lib().ivb_bnb_options_default(ctypes.byref(o))
@@ -308,7 +326,7 @@ class Problem:
             o.split_mode = 1 + (SPLIT[strategy] if isinstance(strategy, str) else int(strategy))
             o.target = int(target)
         o.batch, o.eps_abs, o.eps_rel = int(batch), float(eps_abs), float(eps_rel)
-        o.max_nodes, o.time_limit = int(max_nodes), float(time_limit)
+        o.max_nodes, o.time_limit, o.corner_ub = int(max_nodes), float(time_limit), int(corner_ub)
         r = ivb_bnb_result()
         _check(lib().ivb_bnb_solve(self._h, self.n_vars, _ptr(root), ctypes.byref(o), ctypes.byref(r), None),
                self._h)

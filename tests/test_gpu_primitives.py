@@ -1,0 +1,137 @@
+"""The kernels' interval operations (through the C-ABI test hook ivb_eval_op)
+against the oracle's, on large sets of random and special operands:
++ - * / sqr sqrt and the reciprocal bit for bit (directed rounding is unique);
+exp and log contain the oracle's tight enclosure, each end within 4 ulps."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_20769_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2507_20769_gb300 import build as B  # noqa: E402
+
+B.build()
+from paper_2507_20769_gb300 import ivb  # noqa: E402
+
+DEV = torch.device("cuda:0")
+RECIP = 100
+
+
+def random_doubles(rng, n, emin=-1074, emax=1023, sign=True):
+    """finite doubles with log-uniform magnitudes over [2^emin, 2^emax]"""
+    e = rng.uniform(emin, emax, n)
+    m = rng.uniform(1.0, 2.0, n)
+    v = np.ldexp(m, np.floor(e).astype(np.int64))
+    if sign:
+        v *= rng.choice([-1.0, 1.0], n)
+    return v
+
+
+def specials():
+    tiny = np.nextafter(0.0, 1.0)
+    big = np.finfo(np.float64).max
+    v = [0.0, -0.0, 1.0, -1.0, 2.0, 0.5, 3.0, 1.5, tiny, -tiny, big, -big, 2.0 ** -1022, 2.0 ** 1023,
+         np.nextafter(1.0, 2.0), np.nextafter(1.0, 0.0), np.nextafter(2.0, 0.0), np.nextafter(0.5, 1.0), 1.0 / 3.0]
+    return np.array(v)
+
+
+def intervals(rng, n, emin=-1074, emax=1023, positive=False):
+    a = random_doubles(rng, n, emin, emax, sign=not positive)
+    b = random_doubles(rng, n, emin, emax, sign=not positive)
+    # a third are points (directed rounding of single operations), a third narrow
+    pts = rng.random(n) < 0.33
+    b[pts] = a[pts]
+    nar = (~pts) & (rng.random(n) < 0.5)
+    b[nar] = a[nar] * (1.0 + rng.uniform(-1e-6, 1e-6, nar.sum()))
+    X = np.stack([np.minimum(a, b), np.maximum(a, b)], 1)
+    s = specials()
+    if positive:
+        s = s[s > 0]
+    S = np.array([[p, q] for p in s for q in s if p <= q])
+    return np.concatenate([X, S])
+
+
+def gpu(opcode, X, Y=None):
+    x = torch.from_numpy(np.ascontiguousarray(X)).to(DEV)
+    y = None if Y is None else torch.from_numpy(np.ascontiguousarray(Y)).to(DEV)
+    r = ivb.ivb_eval_op(opcode, x, y)
+    return r.cpu().numpy()
+
+
+@pytest.mark.parametrize("opcode", [W.OP_ADD, W.OP_SUB, W.OP_MUL, W.OP_DIV])
+def test_binary_ops_bit_exact(opcode):
+    rng = np.random.default_rng(opcode)
+    n = 200000
+    X = intervals(rng, n, -540, 500)
+    Y = intervals(rng, n, -540, 500)
+    m = min(len(X), len(Y))
+    X, Y = X[:m], Y[:m]
+    R = gpu(opcode, X, Y)
+    Ro = oracle.iv_op(opcode, X, Y)
+    bad = ~((R == Ro) | (np.isnan(R) & np.isnan(Ro))).all(axis=1)
+    assert not bad.any(), (X[bad][:3], Y[bad][:3], R[bad][:3], Ro[bad][:3])
+
+
+def test_division_exact_and_binade_cases():
+    """quotients that are exact, powers of two, or next to them"""
+    rng = np.random.default_rng(9)
+    y = random_doubles(rng, 20000, -300, 300, sign=False)
+    k = rng.integers(1, 64, y.size).astype(np.float64)
+    xs = [k * y, np.ldexp(y, rng.integers(-20, 20, y.size)), np.nextafter(y, 0) * 2.0, np.nextafter(2 * y, 10 * y)]
+    for x in xs:
+        X = np.stack([x, x], 1)
+        Y = np.stack([y, y], 1)
+        for sgn in (1.0, -1.0):
+            R = gpu(W.OP_DIV, sgn * X, Y)
+            assert np.array_equal(R, oracle.iv_op(W.OP_DIV, sgn * X, Y))
+
+
+@pytest.mark.parametrize("opcode", [W.OP_SQR, W.OP_SQRT, RECIP, W.OP_NEG])
+def test_unary_ops_bit_exact(opcode):
+    rng = np.random.default_rng(50 + opcode)
+    X = intervals(rng, 200000, -1074, 1023, positive=(opcode == W.OP_SQRT))
+    if opcode == RECIP:
+        X = X[(X[:, 0] > 0) | (X[:, 1] < 0)]
+    R = gpu(opcode, X)
+    Ro = oracle.iv_op(opcode, X)
+    bad = ~((R == Ro) | (np.isnan(R) & np.isnan(Ro))).all(axis=1)
+    assert not bad.any(), (X[bad][:3], R[bad][:3], Ro[bad][:3])
+
+
+def ulps(a, b):
+    ia = np.asarray(a, np.float64).view(np.int64)
+    ib = np.asarray(b, np.float64).view(np.int64)
+    ia = np.where(ia < 0, np.int64(-(2 ** 63)) - ia, ia)
+    ib = np.where(ib < 0, np.int64(-(2 ** 63)) - ib, ib)
+    return np.abs(ia - ib)
+
+
+@pytest.mark.parametrize("fn", ["exp", "log"])
+def test_exp_log_contain_oracle_within_4_ulps(fn):
+    rng = np.random.default_rng(77)
+    if fn == "exp":
+        pts = np.concatenate([rng.uniform(-745, 710, 150000), rng.uniform(-1, 1, 50000),
+                              np.ldexp(rng.uniform(-1, 1, 20000), -rng.integers(1, 60, 20000)),
+                              np.array([0.0, -0.0, 700.0, -700.0, 709.7, -745.0, 1e-300])])
+        opcode = W.OP_EXP
+    else:
+        pts = np.concatenate([random_doubles(rng, 150000, -1074, 1023, sign=False),
+                              1.0 + rng.uniform(-0.01, 0.01, 50000), 1.0 + np.ldexp(rng.uniform(-1, 1, 20000), -30),
+                              np.array([1.0, 2.0, 0.5, 1.5, 0.75, np.nextafter(1.0, 0), np.nextafter(1.0, 2)])])
+        opcode = W.OP_LOG
+    X = np.stack([pts, pts], 1)
+    R = gpu(opcode, X)
+    Ro = oracle.iv_op(opcode, X, tight=True)
+    assert np.all(R[:, 0] <= Ro[:, 0]) and np.all(R[:, 1] >= Ro[:, 1])
+    fin = np.isfinite(Ro[:, 0]) & (Ro[:, 0] != 0)
+    assert np.all(ulps(R[fin, 0], Ro[fin, 0]) <= 4)
+    fin = np.isfinite(Ro[:, 1]) & (Ro[:, 1] != 0)
+    assert np.all(ulps(R[fin, 1], Ro[fin, 1]) <= 4)
