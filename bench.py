@@ -248,8 +248,9 @@ def main():
              "own_rcp", "own_div", "own_sqrt", "own_exp", "own_log")
     rates = {k: ivb.ivb_fp64_probe(k) for k in names}
     peak = rates["dfma"]
-    for k in ("log", "own_log"):     # both log probes carry one round-to-nearest add
-        rates[k] = 1.0 / max(1.0 / rates[k] - 1.0 / rates["dadd"], 1e-30)
+    for k, extra in (("log", "dadd"), ("own_log", "dadd"), ("dsqrt", "dmul"), ("own_sqrt", "dmul")):
+        # these probes carry one extra round-to-nearest add / multiply per operation
+        rates[k] = 1.0 / max(1.0 / rates[k] - 1.0 / rates[extra], 1e-30)
     # cost of each category in DFMA issue slots: the primitives the kernel runs
     cost = {"addsub": peak / rates["dadd"], "mul": peak / rates["dmul"], "div": peak / rates["own_div"],
             "rcp": peak / rates["own_rcp"], "sqrt": peak / rates["own_sqrt"], "exp": peak / rates["own_exp"],

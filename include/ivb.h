@@ -263,7 +263,8 @@ ivb_status ivb_op_counts(const ivb_problem* p, int64_t counts[IVB_CNT_N]);
  * CUDA's directed intrinsics and exp/log; OWN_* are the directed primitives
  * this library's kernels use (one directed end each, outward widening of
  * exp/log included) and give the cost of each category of ivb_op_counts in
- * DFMA issue slots. Both LOG probes include one round-to-nearest add. */
+ * DFMA issue slots. Both LOG probes include one round-to-nearest add and both
+ * SQRT probes one round-to-nearest multiply. */
 enum {
     IVB_PROBE_DADD = 0, IVB_PROBE_DMUL = 1, IVB_PROBE_DFMA = 2, IVB_PROBE_DDIV = 3,
     IVB_PROBE_DRCP = 4, IVB_PROBE_DSQRT = 5, IVB_PROBE_EXP = 6, IVB_PROBE_LOG = 7,

@@ -56,6 +56,14 @@ __device__ __forceinline__ double dn1(double y) {   // next toward -inf, y finit
 __device__ __forceinline__ bool sgn_ge0(double x) { long long b = __double_as_longlong(x); return b >= 0 || b == (long long)0x8000000000000000ULL; }
 __device__ __forceinline__ bool sgn_le0(double x) { return __double_as_longlong(x) <= 0 || __double_as_longlong(x) == (long long)0x8000000000000000ULL; }
 
+// Slow paths out of line: inlined, the compiler would start parts of them
+// speculatively on the fast path, which costs FP64 issue slots every call.
+__device__ __noinline__ double rcp_slow(double y, bool up) { return up ? __drcp_ru(y) : __drcp_rd(y); }
+__device__ __noinline__ double div_slow(double x, double y, bool up) { return up ? __ddiv_ru(x, y) : __ddiv_rd(x, y); }
+__device__ __noinline__ double sqrt_slow(double x, bool up) { return up ? __dsqrt_ru(x) : __dsqrt_rd(x); }
+__device__ __noinline__ double exp_slow(double x) { return exp(x); }
+__device__ __noinline__ double log_slow(double x) { return log(x); }
+
 // 1/y seed for y > 0 with biased exponent E in [1, 2044]: relative error < 2^-21
 __device__ __forceinline__ double rcp_seed(double y) {
     const long long b = __double_as_longlong(y);
@@ -85,7 +93,7 @@ __device__ __forceinline__ double rcp_dir_pos(double y, bool up) {
             return (sgn_ge0(rho)) ? r : dn1(r);
         }
     }
-    return up ? __drcp_ru(y) : __drcp_rd(y);
+    return rcp_slow(y, up);
 }
 
 // ---------------------------------------------------------------- division
@@ -111,7 +119,7 @@ __device__ __forceinline__ double div_dir_pos(double x, double y, double r, bool
             return sgn_ge0(rho) ? q : dn1(q);
         }
     }
-    return up ? __ddiv_ru(x, y) : __ddiv_rd(x, y);
+    return div_slow(x, y, up);
 }
 
 // directed reciprocal for y of either sign (y != 0, finite or infinite)
@@ -147,7 +155,7 @@ __device__ __forceinline__ double sqrt_dir(double x, bool up) {
             return sgn_ge0(d) ? g : dn1(g);
         }
     }
-    return up ? __dsqrt_ru(x) : __dsqrt_rd(x);
+    return sqrt_slow(x, up);
 }
 
 // ---------------------------------------------------------------- exp
@@ -216,13 +224,13 @@ __device__ __forceinline__ double log_core(double x, bool* ok) {
 __device__ __forceinline__ double exp_dir(double x, bool up) {
     bool ok;
     double y = exp_core(x, &ok);
-    if (!ok) y = exp(x);
+    if (!ok) y = exp_slow(x);
     return up ? next_up(next_up(y)) : next_dn(next_dn(y));
 }
 __device__ __forceinline__ double log_dir(double x, bool up) {   // x > 0
     bool ok;
     double y = log_core(x, &ok);
-    if (!ok) y = log(x);
+    if (!ok) y = log_slow(x);
     return up ? next_up(next_up(y)) : next_dn(next_dn(y));
 }
 

@@ -116,7 +116,17 @@ __device__ __forceinline__ iv iv_mul(iv x, iv y) {
     return mk(prod_dn(lx, ly), prod_up(ux, uy));
 }
 
-__device__ __forceinline__ iv iv_twice(iv x) { return mk(__dmul_rd(2.0, x.lo), __dmul_ru(2.0, x.hi)); }
+// 2*x rounded toward -inf / +inf: exact (an exponent increment on the integer
+// pipe, or a shift for zero and subnormals) unless |x| >= 2^1023, where the
+// directed multiply decides between the largest double and infinity
+__device__ __forceinline__ double twice_dir(double x, bool up) {
+    const long long b = bits(x);
+    const int E = (int)((b >> 52) & 0x7FF);
+    if (E == 0) return from_bits((b & (long long)0x8000000000000000ULL) | ((b & 0x7FFFFFFFFFFFFFFFLL) << 1));
+    if (E < 2046) return from_bits(b + (1LL << 52));
+    return up ? __dmul_ru(2.0, x) : __dmul_rd(2.0, x);
+}
+__device__ __forceinline__ iv iv_twice(iv x) { return mk(twice_dir(x.lo, false), twice_dir(x.hi, true)); }
 
 __device__ __forceinline__ iv iv_sqr(iv x) {
     if (ge0(x.lo)) return mk(prod_dn(x.lo, x.lo), prod_up(x.hi, x.hi));

@@ -600,7 +600,7 @@ __global__ void k_own_probe(double* out, double seed, int iters) {
         for (int j = 0; j < 8; ++j) {
             if (W == 0) x[j] = rcp_dir_pos(x[j], false);
             if (W == 1) x[j] = div_dir_pos(y, x[j], rcp_refined(x[j]), false);
-            if (W == 2) x[j] = sqrt_dir(x[j], false);
+            if (W == 2) x[j] = sqrt_dir(x[j] * 3.1, false);   // one multiply keeps x off powers of two
             if (W == 3) x[j] = exp_dir(-x[j], false);
             if (W == 4) x[j] = __dadd_rn(log_dir(x[j], false), 2.0);
         }

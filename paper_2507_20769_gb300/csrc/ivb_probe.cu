@@ -20,7 +20,7 @@ __device__ __forceinline__ double step(double x, double y) {
     if (W == IVB_PROBE_DFMA) return __fma_rn(x, y, 1e-300);
     if (W == IVB_PROBE_DDIV) return __ddiv_rd(y, x);
     if (W == IVB_PROBE_DRCP) return __drcp_rd(x);
-    if (W == IVB_PROBE_DSQRT) return __dsqrt_rd(x);
+    if (W == IVB_PROBE_DSQRT) return __dsqrt_rd(x * 3.1);   // times one multiply (keeps x off powers of two)
     if (W == IVB_PROBE_EXP) return exp(-x);
     return __dadd_rn(log(x), 2.0);   // IVB_PROBE_LOG: log plus one add (fixed point near 3.15)
 }
