@@ -43,18 +43,18 @@ __device__ __forceinline__ float rsqrt_approx_f(float x) {
     return r;
 }
 
-__device__ __forceinline__ int bexp(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
-__device__ __forceinline__ bool mant_zero(double x) { return (__double_as_longlong(x) & 0x000FFFFFFFFFFFFFLL) == 0; }
+__device__ __forceinline__ int bexp(double x) { return (int)((bits(x) >> 52) & 0x7FF); }
+__device__ __forceinline__ bool mant_zero(double x) { return (bits(x) & 0x000FFFFFFFFFFFFFLL) == 0; }
 __device__ __forceinline__ double up1(double y) {   // next toward +inf, y finite nonzero
-    long long b = __double_as_longlong(y);
-    return __longlong_as_double(b >= 0 ? b + 1 : b - 1);
+    long long b = bits(y);
+    return from_bits(b >= 0 ? b + 1 : b - 1);
 }
 __device__ __forceinline__ double dn1(double y) {   // next toward -inf, y finite nonzero
-    long long b = __double_as_longlong(y);
-    return __longlong_as_double(b >= 0 ? b - 1 : b + 1);
+    long long b = bits(y);
+    return from_bits(b >= 0 ? b - 1 : b + 1);
 }
-__device__ __forceinline__ bool sgn_ge0(double x) { long long b = __double_as_longlong(x); return b >= 0 || b == (long long)0x8000000000000000ULL; }
-__device__ __forceinline__ bool sgn_le0(double x) { return __double_as_longlong(x) <= 0 || __double_as_longlong(x) == (long long)0x8000000000000000ULL; }
+__device__ __forceinline__ bool sgn_ge0(double x) { long long b = bits(x); return b >= 0 || b == (long long)0x8000000000000000ULL; }
+__device__ __forceinline__ bool sgn_le0(double x) { return bits(x) <= 0 || bits(x) == (long long)0x8000000000000000ULL; }
 
 // Slow paths out of line: inlined, the compiler would start parts of them
 // speculatively on the fast path, which costs FP64 issue slots every call.
@@ -66,13 +66,13 @@ __device__ __noinline__ double log_slow(double x) { return log(x); }
 
 // 1/y seed for y > 0 with biased exponent E in [1, 2044]: relative error < 2^-21
 __device__ __forceinline__ double rcp_seed(double y) {
-    const long long b = __double_as_longlong(y);
+    const long long b = bits(y);
     const int E = (int)((b >> 52) & 0x7FF);
     const float m = __int_as_float(0x3F800000 | (int)((b >> 29) & 0x7FFFFF));   // y's mantissa in [1,2)
     const int rb = __float_as_int(rcp_approx_f(m));                              // (0.5, 1]
     const int fe = (rb >> 23) & 0xFF;
     const long long db = ((long long)(fe - 127 + 2046 - E) << 52) | ((long long)(rb & 0x7FFFFF) << 29);
-    return __longlong_as_double(db);
+    return from_bits(db);
 }
 
 // fast-path exponent window: products, quotients and remainders stay normal
@@ -108,8 +108,8 @@ __device__ __forceinline__ double rcp_refined(double y) {
 // correctly rounded x/y toward -inf or +inf, y > 0, given r = rcp_refined(y)
 __device__ __forceinline__ double div_dir_pos(double x, double y, double r, bool up) {
     const int Ex = bexp(x), Ey = bexp(y);
-    const bool x0 = (__double_as_longlong(x) << 1) == 0;
-    if (__double_as_longlong(r) != 0 && (x0 || (safe_e(Ex) && Ex - Ey <= 900 && Ey - Ex <= 900))) {
+    const bool x0 = (bits(x) << 1) == 0;
+    if (bits(r) != 0 && (x0 || (safe_e(Ex) && Ex - Ey <= 900 && Ey - Ex <= 900))) {
         if (x0) return x * r;                          // exact +-0
         const double q0 = x * r;
         const double q = __fma_rn(__fma_rn(-y, q0, x), r, q0);   // within 0.5 ulp + 2^-80 relative
@@ -124,16 +124,16 @@ __device__ __forceinline__ double div_dir_pos(double x, double y, double r, bool
 
 // directed reciprocal for y of either sign (y != 0, finite or infinite)
 __device__ __forceinline__ double rcp_dn(double y) {
-    return __double_as_longlong(y) > 0 ? rcp_dir_pos(y, false) : -rcp_dir_pos(-y, true);
+    return bits(y) > 0 ? rcp_dir_pos(y, false) : ineg(rcp_dir_pos(ineg(y), true));
 }
 __device__ __forceinline__ double rcp_up(double y) {
-    return __double_as_longlong(y) > 0 ? rcp_dir_pos(y, true) : -rcp_dir_pos(-y, false);
+    return bits(y) > 0 ? rcp_dir_pos(y, true) : ineg(rcp_dir_pos(ineg(y), false));
 }
 
 // ---------------------------------------------------------------- square root
 // correctly rounded sqrt(x) toward -inf or +inf, x >= 0
 __device__ __forceinline__ double sqrt_dir(double x, bool up) {
-    const long long b = __double_as_longlong(x);
+    const long long b = bits(x);
     const int E = (int)((b >> 52) & 0x7FF);
     if (safe_e(E)) {
         // x = m 2^e, e = E - 1023; seed for 1/sqrt of m' = m or 2m so that the exponent halves
@@ -142,9 +142,9 @@ __device__ __forceinline__ double sqrt_dir(double x, bool up) {
         const int rb = __float_as_int(rsqrt_approx_f(mf));
         const int fe = (rb >> 23) & 0xFF;
         const int h = (E - 1023 - odd) / 2;          // exact: E - 1023 - odd is even
-        const double r0 = __longlong_as_double(((long long)(fe - 127 - h + 1023) << 52) | ((long long)(rb & 0x7FFFFF) << 29));
+        const double r0 = from_bits(((long long)(fe - 127 - h + 1023) << 52) | ((long long)(rb & 0x7FFFFF) << 29));
         double g = x * r0;                           // ~sqrt(x)
-        double hh = __longlong_as_double(__double_as_longlong(r0) - (1LL << 52));   // r0 / 2, exact
+        double hh = from_bits(bits(r0) - (1LL << 52));   // r0 / 2, exact
         const double eps = __fma_rn(-g, hh, 0.5);
         g = __fma_rn(g, eps, g);
         hh = __fma_rn(hh, eps, hh);
@@ -161,12 +161,12 @@ __device__ __forceinline__ double sqrt_dir(double x, bool up) {
 // ---------------------------------------------------------------- exp
 // double whose value is the integer k (|k| < 2^31), one FP64 add
 __device__ __forceinline__ double int_to_double(int k) {
-    return __longlong_as_double(0x4338000000000000LL + (long long)k) - 6755399441055744.0;
+    return from_bits(0x4338000000000000LL + (long long)k) - 6755399441055744.0;
 }
 
 // exp(x) for |x| <= 700 (fast path): one final rounding plus < 2^-59 relative
 __device__ __forceinline__ double exp_core(double x, bool* ok) {
-    const long long b = __double_as_longlong(x);
+    const long long b = bits(x);
     const int E = (int)((b >> 52) & 0x7FF);
     if ((b & 0x7FFFFFFFFFFFFFFFLL) > 0x4085E00000000000LL) { *ok = false; return 0.0; }   // |x| > 700
     *ok = true;
@@ -189,12 +189,12 @@ __device__ __forceinline__ double exp_core(double x, bool* ok) {
     const int j = k & 127, m = k >> 7;
     const double th = g_math.exp_hi[j], tl = g_math.exp_lo[j];
     const double y = th + __fma_rn(th, p, tl);       // 2^(j/128) (1 + p), one final rounding
-    return __longlong_as_double(__double_as_longlong(y) + ((long long)m << 52));
+    return from_bits(bits(y) + ((long long)m << 52));
 }
 
 // log(x) for normal x > 0 (fast path), error below 1.5 ulp of the result
 __device__ __forceinline__ double log_core(double x, bool* ok) {
-    const long long b = __double_as_longlong(x);
+    const long long b = bits(x);
     const int E = (int)((b >> 52) & 0x7FF);
     if (b <= 0 || E == 0 || E == 0x7FF) { *ok = false; return 0.0; }
     *ok = true;
@@ -203,7 +203,7 @@ __device__ __forceinline__ double log_core(double x, bool* ok) {
     const int j = (int)(mant >> 44);                 // top 8 mantissa bits
     long long yb = 0x3FF0000000000000LL | mant;       // y in [1, 2)
     if (j >= 128) { yb -= (1LL << 52); m += 1; }      // y in [0.75, 1)
-    const double y = __longlong_as_double(yb);
+    const double y = from_bits(yb);
     const double r = __fma_rn(y, g_math.log_c[j], -1.0);   // |r| <= 2^-8
     // log1p(r) = r + r^2 P(r), P to degree 5: truncation below 2^-66
     double P = __fma_rn(r, 1.0 / 7.0, -1.0 / 6.0);

@@ -22,8 +22,21 @@ struct iv {
     double lo, hi;
 };
 
-__device__ __forceinline__ long long bits(double x) { return __double_as_longlong(x); }
-__device__ __forceinline__ double from_bits(long long b) { return __longlong_as_double(b); }
+// Bit-pattern views of a double. The moves are written in PTX so that the
+// compiler does not recognise the integer operations on the pattern (sign
+// flips, zero and sign tests, magnitude masks) and turn them back into FP64
+// negations, compares or absolute values, which would each take an issue
+// slot of the narrow FP64 pipe.
+__device__ __forceinline__ long long bits(double x) {
+    long long b;
+    asm("mov.b64 %0, %1;" : "=l"(b) : "d"(x));
+    return b;
+}
+__device__ __forceinline__ double from_bits(long long b) {
+    double x;
+    asm("mov.b64 %0, %1;" : "=d"(x) : "l"(b));
+    return x;
+}
 
 // x >= 0 (includes -0), x <= 0 (includes +0), x == 0 (either sign); no NaNs
 __device__ __forceinline__ bool ge0(double x) {
@@ -85,7 +98,7 @@ __device__ __forceinline__ double prod_up(double x, double y) {
 
 // ---------------------------------------------------------------- intervals
 __device__ __forceinline__ iv mk(double lo, double hi) { iv r; r.lo = lo; r.hi = hi; return r; }
-__device__ __forceinline__ iv entire() { return mk(-__longlong_as_double(0x7FF0000000000000LL), __longlong_as_double(0x7FF0000000000000LL)); }
+__device__ __forceinline__ iv entire() { return mk(from_bits((long long)0xFFF0000000000000ULL), from_bits(0x7FF0000000000000LL)); }
 __device__ __forceinline__ iv zero() { return mk(0.0, 0.0); }
 __device__ __forceinline__ iv one() { return mk(1.0, 1.0); }
 __device__ __forceinline__ bool has_inf(iv x) { return isinf_(x.lo) || isinf_(x.hi); }
@@ -95,25 +108,31 @@ __device__ __forceinline__ iv iv_sub(iv x, iv y) { return mk(sub_dn(x.lo, y.hi),
 __device__ __forceinline__ iv iv_neg(iv x) { return mk(ineg(x.hi), ineg(x.lo)); }
 
 // product: sign-case choice of the endpoint pairs that realise min and max of
-// the four endpoint products (P: lo >= 0, N: hi <= 0, M: otherwise)
+// the four endpoint products (P: lo >= 0, N: hi <= 0, M: otherwise). The
+// operands are picked with selects on the integer pipe, so every lane issues
+// the same two directed multiplies; lanes where both factors straddle 0 need a
+// second pair, issued only when some lane of the warp needs it (warp-uniform
+// branch: no FP64 instruction runs with idle lanes for the common case).
 __device__ __forceinline__ iv iv_mul(iv x, iv y) {
     const bool xP = ge0(x.lo), xN = !xP && le0(x.hi), xM = !xP && !xN;
     const bool yP = ge0(y.lo), yN = !yP && le0(y.hi), yM = !yP && !yN;
-    if (xM && yM) {
-        double lo = imin(prod_dn(x.lo, y.hi), prod_dn(x.hi, y.lo));
-        double hi = imax(prod_up(x.lo, y.lo), prod_up(x.hi, y.hi));
-        return mk(lo, hi);
-    }
+    const bool mm = xM && yM;
     // endpoint pairs (lower | upper):
     //   P,P: lo*lo | hi*hi   P,M: hi*lo | hi*hi   P,N: hi*lo | lo*hi
-    //   M,P: lo*hi | hi*hi   M,N: hi*lo | lo*lo
+    //   M,P: lo*hi | hi*hi   M,N: hi*lo | lo*lo   M,M: lo*hi, hi*lo | lo*lo, hi*hi
     //   N,P: lo*hi | hi*lo   N,M: lo*hi | lo*lo   N,N: hi*hi | lo*lo
-    const double lx = (xP ? !yP : yN) ? x.hi : x.lo;
-    const double ly = (xP || (xM && yN)) ? y.lo : y.hi;
-    const double ux = (xP ? !yN : yP) ? x.hi : x.lo;
-    const double uy = (xP || (xM && yP)) ? y.hi : y.lo;
-    (void)yM;
-    return mk(prod_dn(lx, ly), prod_up(ux, uy));
+    const double lx = mm ? x.lo : ((xP ? !yP : yN) ? x.hi : x.lo);
+    const double ly = mm ? y.hi : ((xP || (xM && yN)) ? y.lo : y.hi);
+    const double ux = mm ? x.lo : ((xP ? !yN : yP) ? x.hi : x.lo);
+    const double uy = mm ? y.lo : ((xP || (xM && yP)) ? y.hi : y.lo);
+    double lo = prod_dn(lx, ly), hi = prod_up(ux, uy);
+    if (__any_sync(__activemask(), mm)) {
+        const double lo2 = prod_dn(mm ? x.hi : lx, mm ? y.lo : ly);
+        const double hi2 = prod_up(mm ? x.hi : ux, mm ? y.hi : uy);
+        lo = imin(lo, lo2);
+        hi = imax(hi, hi2);
+    }
+    return mk(lo, hi);
 }
 
 // 2*x rounded toward -inf / +inf: exact (an exponent increment on the integer
@@ -128,12 +147,14 @@ __device__ __forceinline__ double twice_dir(double x, bool up) {
 }
 __device__ __forceinline__ iv iv_twice(iv x) { return mk(twice_dir(x.lo, false), twice_dir(x.hi, true)); }
 
+// square: [a^2, b^2] with b = max(|lo|, |hi|) and a = min(|lo|, |hi|), or
+// a = 0 when the interval straddles 0 -- two directed multiplies, no branch
 __device__ __forceinline__ iv iv_sqr(iv x) {
-    if (ge0(x.lo)) return mk(prod_dn(x.lo, x.lo), prod_up(x.hi, x.hi));
-    if (le0(x.hi)) return mk(prod_dn(x.hi, x.hi), prod_up(x.lo, x.lo));
-    // straddles zero: upper end from the endpoint of larger magnitude
-    const double m = (bits(x.lo) & 0x7FFFFFFFFFFFFFFFLL) > (bits(x.hi) & 0x7FFFFFFFFFFFFFFFLL) ? x.lo : x.hi;
-    return mk(0.0, prod_up(m, m));
+    const long long ml = bits(x.lo) & 0x7FFFFFFFFFFFFFFFLL, mh = bits(x.hi) & 0x7FFFFFFFFFFFFFFFLL;
+    const bool straddle = !ge0(x.lo) && !le0(x.hi);
+    const double big = from_bits(ml > mh ? ml : mh);
+    const double small = straddle ? 0.0 : from_bits(ml > mh ? mh : ml);
+    return mk(prod_dn(small, small), prod_up(big, big));
 }
 
 // reciprocal of an interval without 0 (ENTIRE otherwise)

@@ -231,13 +231,13 @@ __device__ __forceinline__ unsigned long long ukey(double x) {
     return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
 }
 __device__ __forceinline__ unsigned long long ukey_lo(double x) {   // NaN -> -inf
-    return isnan_(x) ? ukey(-__longlong_as_double(0x7FF0000000000000LL)) : ukey(x);
+    return isnan_(x) ? ukey(from_bits((long long)0xFFF0000000000000ULL)) : ukey(x);
 }
 __device__ __forceinline__ unsigned long long ukey_hi(double x) {   // NaN -> +inf
-    return isnan_(x) ? ukey(__longlong_as_double(0x7FF0000000000000LL)) : ukey(x);
+    return isnan_(x) ? ukey(from_bits(0x7FF0000000000000LL)) : ukey(x);
 }
 __device__ __forceinline__ double unkey(unsigned long long k) {
-    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFULL) : ~k));
+    return from_bits((long long)((k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFULL) : ~k));
 }
 
 __device__ __forceinline__ unsigned long long shfl_xor64(unsigned long long v, int m) {
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(512) k_bound(const KParams P) {
             }
             // ---- Step 2b: gradient enclosures and the Mean Value Form, output by output
             bool cert_infeasible = false;
-            double obj_lo = __longlong_as_double(0x7FF0000000000000LL);
+            double obj_lo = from_bits(0x7FF0000000000000LL);
             if (MODE == KM_FWD_REDUCE || MODE == KM_FWD_STORE) {
                 if (valid) run_tangents(G.ins + G.tan_begin, G.tan_count, C, L.phase_base, n);
             }
@@ -414,13 +414,13 @@ __global__ void __launch_bounds__(512) k_bound(const KParams P) {
             }
             if (MODE == KM_FWD_REDUCE || MODE == KM_ADJ_REDUCE) {
                 // certified-feasible centre upper bound and filtered objective minimum
-                double ub = __longlong_as_double(0x7FF0000000000000LL);
+                double ub = from_bits(0x7FF0000000000000LL);
                 if (valid) {
                     bool feas = !G.has_eq;
                     for (int o = 0; o < n_out; ++o)
                         if (G.out_kind[o] == OUT_INEQ && !le0(C.F.ld(L.fc_base + 2 * o + 1))) feas = false;
                     if (feas) ub = C.F.ld(L.fc_base + 2 * G.obj + 1);
-                    if (cert_infeasible) obj_lo = __longlong_as_double(0x7FF0000000000000LL);
+                    if (cert_infeasible) obj_lo = from_bits(0x7FF0000000000000LL);
                 }
                 reduce_key(P.keys, node, 2 * n_out, K, ukey_hi(ub), valid, uniform, true);
                 reduce_key(P.keys, node, 2 * n_out + 1, K, ukey_lo(obj_lo), valid, uniform, true);
