@@ -13,22 +13,25 @@
 // (where the spacing of doubles changes), take the CUDA intrinsic.
 //
 // exp and log (Tang's table-driven method, ACM TOMS 15(2) 1989 and 16(4)
-// 1990): exp(x) = 2^m 2^(j/128) e^r with |r| <= ln2/256 and a degree-5
-// polynomial; log(x) = m ln2 - log(c_j) + log1p(x 2^-m c_j - 1) with 256
-// reciprocal centres c_j and a degree-7 polynomial. Tables are double-double,
-// computed on the host in extended precision. Error before widening below 1.5
-// ulp of the result; the interval ends are then moved two neighbour steps
-// outward, which encloses the true value.
+// 1990): exp(x) = 2^m 2^(j/512) e^r with |r| < 0.0008 and a degree-4
+// polynomial; log(x) = m ln2 - log(c_j) + log1p(x 2^-m c_j - 1) with 2048
+// reciprocal centres c_j and a degree-5 polynomial. Large tables (read
+// through L1) buy short polynomials, i.e. fewer FP64 instructions. Tables are
+// double-double, computed on the host in extended precision. Error before
+// widening below 1.5 ulp of the result; the interval ends are then moved two
+// neighbour steps outward, which encloses the true value.
 #pragma once
 #include <cstdint>
 
 namespace ivb {
 
 // tables, in device memory of this module (filled by init_math_tables)
+constexpr int kExpTab = 512, kLogTab = 2048;
+struct ExpEntry { double hi, lo; };            // 2^(j/512) as hi + lo
+struct LogEntry { double c, hi, lo, pad; };    // reciprocal centre c_j, -log(c_j) as hi + lo
 struct MathTables {
-    double exp_hi[128], exp_lo[128];   // 2^(j/128) as hi + lo
-    double log_c[256];                 // reciprocal centres c_j
-    double log_hi[256], log_lo[256];   // -log(c_j) as hi + lo
+    ExpEntry exp[kExpTab];
+    LogEntry log[kLogTab];
 };
 static __device__ MathTables g_math;
 
@@ -110,7 +113,7 @@ __device__ __forceinline__ double div_dir_pos(double x, double y, double r, bool
     const int Ex = bexp(x), Ey = bexp(y);
     const bool x0 = (bits(x) << 1) == 0;
     if (bits(r) != 0 && (x0 || (safe_e(Ex) && Ex - Ey <= 900 && Ey - Ex <= 900))) {
-        if (x0) return x * r;                          // exact +-0
+        if (x0) return x;                              // exact: +-0 / y = +-0 for y > 0
         const double q0 = x * r;
         const double q = __fma_rn(__fma_rn(-y, q0, x), r, q0);   // within 0.5 ulp + 2^-80 relative
         if (!mant_zero(q)) {
@@ -164,31 +167,30 @@ __device__ __forceinline__ double int_to_double(int k) {
     return from_bits(0x4338000000000000LL + (long long)k) - 6755399441055744.0;
 }
 
-// exp(x) for |x| <= 700 (fast path): one final rounding plus < 2^-59 relative
+// exp(x) for |x| <= 700 (fast path): one final rounding plus < 2^-58 relative
 __device__ __forceinline__ double exp_core(double x, bool* ok) {
     const long long b = bits(x);
     const int E = (int)((b >> 52) & 0x7FF);
     if ((b & 0x7FFFFFFFFFFFFFFFLL) > 0x4085E00000000000LL) { *ok = false; return 0.0; }   // |x| > 700
     *ok = true;
-    // k = round(x 128/ln2), from a float copy of x (any k within one of the rounded value works)
+    // k = round(x 512/ln2), from a float copy of x (any k within one of the rounded value works)
     float xf = 0.0f;
     if (E >= 1023 - 100) xf = __int_as_float((int)((b >> 32) & 0x80000000) | ((E - 1023 + 127) << 23) | (int)((b >> 29) & 0x7FFFFF));
-    const int k = __float2int_rn(xf * 184.66496523378731f);
+    const int k = __float2int_rn(xf * 738.65986f);
     const double kd = int_to_double(k);
-    // r = x - k ln2/128 with ln2/128 = C1 + C2: C1 is ln2/128 rounded to 33 significant
-    // bits (k C1 is exact for |k| < 2^17), C2 the remainder rounded to nearest
-    const double C1 = 0x1.62e42ff000000p-8, C2 = -0x1.718432a1b0e26p-42;
+    // r = x - k ln2/512 with ln2/512 = C1 + C2: C1 is ln2/512 rounded to 32 significant
+    // bits (k C1 is exact for |k| < 2^19), C2 the remainder rounded to nearest
+    const double C1 = 0x1.62e42ff000000p-10, C2 = -0x1.718432a1b0e26p-44;
     double r = __fma_rn(-kd, C1, x);
     r = __fma_rn(-kd, C2, r);
-    // p = e^r - 1, |r| < 0.0028: truncation below 2^-60
-    double u = __fma_rn(r, 1.0 / 120.0, 1.0 / 24.0);
-    u = __fma_rn(r, u, 1.0 / 6.0);
+    // p = e^r - 1, |r| < 0.0008: truncation below 2^-58
+    double u = __fma_rn(r, 1.0 / 24.0, 1.0 / 6.0);
     u = __fma_rn(r, u, 0.5);
     u = __fma_rn(r, u, 1.0);
     const double p = r * u;
-    const int j = k & 127, m = k >> 7;
-    const double th = g_math.exp_hi[j], tl = g_math.exp_lo[j];
-    const double y = th + __fma_rn(th, p, tl);       // 2^(j/128) (1 + p), one final rounding
+    const int j = k & (kExpTab - 1), m = k >> 9;
+    const double th = g_math.exp[j].hi, tl = g_math.exp[j].lo;
+    const double y = th + __fma_rn(th, p, tl);       // 2^(j/512) (1 + p), one final rounding
     return from_bits(bits(y) + ((long long)m << 52));
 }
 
@@ -200,23 +202,24 @@ __device__ __forceinline__ double log_core(double x, bool* ok) {
     *ok = true;
     int m = E - 1023;
     const long long mant = b & 0x000FFFFFFFFFFFFFLL;
-    const int j = (int)(mant >> 44);                 // top 8 mantissa bits
+    const int j = (int)(mant >> 41);                 // top 11 mantissa bits
     long long yb = 0x3FF0000000000000LL | mant;       // y in [1, 2)
-    if (j >= 128) { yb -= (1LL << 52); m += 1; }      // y in [0.75, 1)
+    if (j >= kLogTab / 2) { yb -= (1LL << 52); m += 1; }   // y in [0.75, 1)
     const double y = from_bits(yb);
-    const double r = __fma_rn(y, g_math.log_c[j], -1.0);   // |r| <= 2^-8
-    // log1p(r) = r + r^2 P(r), P to degree 5: truncation below 2^-66
-    double P = __fma_rn(r, 1.0 / 7.0, -1.0 / 6.0);
-    P = __fma_rn(r, P, 1.0 / 5.0);
-    P = __fma_rn(r, P, -0.25);
+    const LogEntry& T = g_math.log[j];
+    const double r = __fma_rn(y, T.c, -1.0);          // |r| <= 2^-11
+    // log1p(r) = r + r^2 P(r), P to degree 3: relative truncation below 2^-57
+    // (next to 1, where r = y - 1 exactly and the result is about r) and below
+    // 2^-62 elsewhere, where the result is at least 2^-11.3 in magnitude
+    double P = __fma_rn(r, 0.2, -0.25);
     P = __fma_rn(r, P, 1.0 / 3.0);
     P = __fma_rn(r, P, -0.5);
     const double md = int_to_double(m);
     // ln2 = LN2_HI + LN2_LO: LN2_HI is ln2 rounded to 42 significant bits (m LN2_HI is
     // exact for |m| < 2^11), LN2_LO the remainder rounded to nearest
     const double LN2_HI = 0x1.62e42fefa3800p-1, LN2_LO = 0x1.ef35793c76730p-45;
-    const double hi = __fma_rn(md, LN2_HI, g_math.log_hi[j]);
-    const double lo = __fma_rn(md, LN2_LO, g_math.log_lo[j]);
+    const double hi = __fma_rn(md, LN2_HI, T.hi);
+    const double lo = __fma_rn(md, LN2_LO, T.lo);
     const double s = __fma_rn(r * r, P, r) + lo;
     return hi + s;
 }

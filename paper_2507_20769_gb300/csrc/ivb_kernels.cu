@@ -647,23 +647,26 @@ cudaError_t init_math_tables() {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 256 && done[dev]) return cudaSuccess;
-    MathTables h;
-    for (int j = 0; j < 128; ++j) {
-        const long double v = exp2l((long double)j / 128.0L);
-        h.exp_hi[j] = (double)v;
-        h.exp_lo[j] = (double)(v - (long double)h.exp_hi[j]);
+    static MathTables h;
+    for (int j = 0; j < kExpTab; ++j) {
+        const long double v = exp2l((long double)j / kExpTab);
+        h.exp[j].hi = (double)v;
+        h.exp[j].lo = (double)(v - (long double)h.exp[j].hi);
     }
-    for (int j = 0; j < 256; ++j) {
-        // y in [1 + j/256, 1 + (j+1)/256); j >= 128 is folded to y/2 in [0.75, 1)
+    const long double T = kLogTab;
+    for (int j = 0; j < kLogTab; ++j) {
+        // y in [1 + j/T, 1 + (j+1)/T); the upper half is folded to y/2 in [0.75, 1);
+        // the two intervals next to 1 use c = 1 so that r = y - 1 is exact
         double c = 1.0;
-        if (j != 0 && j != 255) {
-            const long double F = (j < 128) ? 1.0L + (j + 0.5L) / 256.0L : (1.0L + (j + 0.5L) / 256.0L) / 2.0L;
+        if (j != 0 && j != kLogTab - 1) {
+            const long double F = (j < kLogTab / 2) ? 1.0L + (j + 0.5L) / T : (1.0L + (j + 0.5L) / T) / 2.0L;
             c = (double)(1.0L / F);
         }
         const long double L = -logl((long double)c);
-        h.log_c[j] = c;
-        h.log_hi[j] = (double)L;
-        h.log_lo[j] = (double)(L - (long double)h.log_hi[j]);
+        h.log[j].c = c;
+        h.log[j].hi = (double)L;
+        h.log[j].lo = (double)(L - (long double)h.log[j].hi);
+        h.log[j].pad = 0.0;
     }
     e = cudaMemcpyToSymbol(g_math, &h, sizeof(h));
     if (e == cudaSuccess && dev >= 0 && dev < 256) done[dev] = true;
