@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--bnb", type=int, default=1, help="run the B&B time-to-gap comparison (rank 0)")
     ap.add_argument("--bnb-time", type=float, default=45.0, help="time cap per B&B run, seconds")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target oracle sample time")
+    ap.add_argument("--patterns", type=int, default=1,
+                    help="also time adjoint vs forward (configuration 4) and batched vs per-node (configuration 3)")
     return ap.parse_args()
 
 
@@ -290,6 +292,9 @@ def main():
                                           "adjoint gradients, fast exp/log mode)"}
     if rank == 0 and world == 1 and args.bnb:
         line["bnb"] = bnb_compare(t, wl, args.bnb_time)
+    if rank == 0 and world == 1 and args.patterns:
+        line["differentiation"] = differentiation_compare()
+        line["batching"] = batching_compare()
     p.destroy()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -315,6 +320,60 @@ def traffic_for(subs_step):
     if rec.get("kernel_sha256") != h.hexdigest():
         return None
     return rec["dram_bytes_per_subdomain"] * subs_step
+
+
+def _timed(fn, reps=2):
+    import torch
+    fn()                                   # warm-up (includes autotuning on first use)
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        best = min(best, time.perf_counter() - t0)
+    return best
+
+
+def differentiation_compare():
+    """configuration 4: n = 16, one 400-entry objective, one node of 2^20
+    subdomains per launch: reverse-mode interval adjoints vs forward tangents"""
+    from paper_2507_20769_gb300 import ivb
+    from paper_2507_20769_gb300 import workloads as W
+    wl = W.config_workload(4)
+    t = wl.tape
+    boxes = t.root_box[None].copy()
+    splits = wl.splits[None].astype(np.int32)
+    res = {"subdomains": int(np.prod(wl.splits.astype(np.int64))), "n_vars": t.n_vars, "tape_entries": t.n_ops}
+    for gm in ("adjoint", "forward"):
+        with ivb.Problem(t, grad_mode=gm) as p:
+            sec = _timed(lambda: p.bound_nodes(boxes, splits))
+            res[gm] = {"seconds": sec, "subdomains_per_s": res["subdomains"] / sec,
+                       "endpoint_ops_per_subdomain": sum(p.op_counts().values())}
+    res["adjoint_speedup"] = res["forward"]["seconds"] / res["adjoint"]["seconds"]
+    return res
+
+
+def batching_compare():
+    """configuration 3: 256 nodes of uneven widths (n = 6, objective + 5
+    constraints of 150 entries), per-node subdomain counts 2^10..2^20 from the
+    adaptive picker: one persistent launch (CUDA graph) vs one launch per node"""
+    from paper_2507_20769_gb300 import ivb
+    from paper_2507_20769_gb300 import workloads as W
+    t = W.config_tape(3)
+    boxes, targets = W.uneven_nodes(t.n_vars, 256, t.root_box, seed=W.config_seed(3) + 5)
+    ref_w = t.root_box[:, 1] - t.root_box[:, 0]
+    splits = np.stack([ivb.ivb_pick_splits(b, int(tg), "adaptive", ref_w) for b, tg in zip(boxes, targets)])
+    S = int(np.prod(splits.astype(np.int64), axis=1).sum())
+    res = {"nodes": 256, "subdomains": S}
+    for name, opts in (("batched_adjoint", dict(grad_mode="adjoint", batched=1)),
+                       ("batched_forward", dict(grad_mode="forward", batched=1)),
+                       ("per_node_forward", dict(grad_mode="forward", batched=0))):
+        with ivb.Problem(t, max_nodes=256, **opts) as p:
+            sec = _timed(lambda: p.bound_nodes(boxes, splits), reps=1)
+            res[name] = {"seconds": sec, "subdomain_bounds_per_s": S * t.n_out / sec}
+    res["speedup_vs_per_node_forward"] = res["per_node_forward"]["seconds"] / res["batched_adjoint"]["seconds"]
+    return res
 
 
 def bnb_compare(t, wl, cap):
