@@ -20,6 +20,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ivb_oracle.c")
 _SO = os.path.join(_HERE, "libivb_oracle.so")
+# tests that plant a mistake in a copy of the oracle point this at the copy's build
+_SO_OVERRIDE = os.environ.get("IVB_ORACLE_SO")
 
 GRAD = {"forward": 0, "adjoint": 1}
 FORM = {"mvf": 0, "nie": 1, "mvf_nie": 2}
@@ -28,16 +30,22 @@ STRATEGY = {"uniform": 0, "largest": 1, "adaptive": 2}
 _lib = None
 
 
+def compile_source(src: str, out: str) -> str:
+    """gcc with the oracle's strict IEEE flags"""
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp",
+           "-frounding-math", "-fno-fast-math", "-ffp-contract=off", "-fno-math-errno",
+           "-fsignaling-nans", "-Wall", "-Wno-unknown-pragmas", src, "-o", out, "-lm"]
+    if platform.machine() in ("x86_64", "AMD64", "i686"):
+        cmd.append("-lquadmath")
+    subprocess.run(cmd, check=True)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle into oracle/libivb_oracle.so (strict IEEE flags)."""
     if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
         return _SO
-    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp",
-           "-frounding-math", "-fno-fast-math", "-ffp-contract=off", "-fno-math-errno",
-           "-fsignaling-nans", "-Wall", "-Wno-unknown-pragmas", _SRC, "-o", _SO + ".tmp", "-lm"]
-    if platform.machine() in ("x86_64", "AMD64", "i686"):
-        cmd.append("-lquadmath")
-    subprocess.run(cmd, check=True)
+    compile_source(_SRC, _SO + ".tmp")
     os.replace(_SO + ".tmp", _SO)
     return _SO
 
@@ -45,8 +53,11 @@ def build(force: bool = False) -> str:
 def lib() -> ctypes.CDLL:
     global _lib
     if _lib is None:
-        build()
-        L = ctypes.CDLL(_SO)
+        if _SO_OVERRIDE:
+            L = ctypes.CDLL(_SO_OVERRIDE)
+        else:
+            build()
+            L = ctypes.CDLL(_SO)
         P = ctypes.c_void_p
         I, I64, D = ctypes.c_int, ctypes.c_int64, ctypes.c_double
         L.orc_decode.argtypes = [I, P, P, I64, P, P]
