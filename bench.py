@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--bnb", type=int, default=1, help="run the B&B time-to-gap comparison (rank 0)")
     ap.add_argument("--bnb-time", type=float, default=45.0, help="time cap per B&B run, seconds")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target oracle sample time")
+    ap.add_argument("--specialize", type=int, default=1,
+                    help="1: tape-specialised bounding kernel (NVRTC at problem creation); 0: tape interpreter")
     ap.add_argument("--patterns", type=int, default=1,
                     help="also time adjoint vs forward (configuration 4) and batched vs per-node (configuration 3)")
     return ap.parse_args()
@@ -195,7 +197,7 @@ def main():
     n_nodes = boxes.shape[0]
     subs_step = int(np.prod(splits.astype(np.int64), axis=1).sum())
     units_step = subs_step * t.n_out
-    p = ivb.Problem(t, grad_mode="adjoint", batched=1, use_graph=1, autotune=1)
+    p = ivb.Problem(t, grad_mode="adjoint", batched=1, use_graph=1, autotune=1, specialize=args.specialize)
     boxes_d = torch.from_numpy(boxes).to(dev)
     splits_d = torch.from_numpy(splits).to(dev)
     out = {"lb": torch.empty(n_nodes, dtype=torch.float64, device=dev),
@@ -267,7 +269,8 @@ def main():
     step_s = t_local / args.steps
     achieved = slots_per_sub * subs_step / step_s
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
-                "unit": "G FP64 DFMA-slot/s", "frac": achieved / peak, "traffic": traffic_for(subs_step),
+                "unit": "G FP64 DFMA-slot/s", "frac": achieved / peak,
+                "traffic": traffic_for(subs_step, "specialised" if args.specialize else "interpreter"),
                 "peak_source": "measured live: DFMA lane-op/s of this GPU (ivb_fp64_probe), "
                                f"= {2 * peak / 1e12:.3f} FP64 TFLOP/s",
                 "work_per_subdomain": {"endpoint_ops": ops_per_sub, "dfma_slots": slots_per_sub,
@@ -283,13 +286,16 @@ def main():
             "config": workload_desc(args.nodes, world), "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches), "clocks": clk,
-            "subdomains_per_s": value / t.n_out, "tuning": p.get_tuning()}
+            "subdomains_per_s": value / t.n_out, "tuning": p.get_tuning(),
+            "kernel": kernel_desc(p)}
 
     if rank == 0 and world == 1:
         rate, C, cores, secs = oracle_rate(t, boxes[0], splits[0], args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"first {C} of the 65536 subdomains of node 0 ({secs:.1f} s; "
                                           "adjoint gradients, fast exp/log mode)"}
+    if rank == 0 and world == 1 and args.specialize:
+        line["interpreter"] = interpreter_compare(t, boxes_d, splits_d, out, flush, stream, subs_step, step_s)
     if rank == 0 and world == 1 and args.bnb:
         line["bnb"] = bnb_compare(t, wl, args.bnb_time)
     if rank == 0 and world == 1 and args.patterns:
@@ -303,21 +309,64 @@ def main():
     return 0
 
 
-def traffic_for(subs_step):
-    """DRAM bytes per launch of the bounding kernel from the committed ncu
-    summary, scaled by subdomains, while the kernel source is the one that
-    was profiled; None otherwise"""
+def kernel_desc(p):
+    s = p.get_specialization()
+    if not s["active"]:
+        return {"bounding_kernel": "tape interpreter (ivb::k_bound)"}
+    return {"bounding_kernel": "tape-specialised (ivb_jit_bound, NVRTC sm_103a at problem creation)",
+            "registers": s["registers"], "local_bytes": s["local_bytes"],
+            "compile_seconds": round(s["compile_seconds"], 2)}
+
+
+def interpreter_compare(t, boxes_d, splits_d, out, flush, stream, subs_step, step_s):
+    """the same step through the tape interpreter (bit-identical bounds), for context"""
+    import torch
+    from paper_2507_20769_gb300 import ivb
+    p = ivb.Problem(t, grad_mode="adjoint", batched=1, use_graph=1, autotune=1, specialize=0)
+    for _ in range(3):
+        p.bound_nodes_ex(boxes_d, splits_d, out=out)
+    ms = []
+    for _ in range(3):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        p.bound_nodes_ex(boxes_d, splits_d, out=out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    p.destroy()
+    m = float(np.median(ms))
+    return {"ms_per_step": m, "subdomains_per_s": subs_step / (m / 1e3),
+            "specialised_speedup": m / (1e3 * step_s)}
+
+
+# source files each bounding kernel is built from (the traffic record is valid
+# only while they are unchanged)
+KERNEL_SOURCES = {
+    "interpreter": ("ivb_kernels.cu", "ivb_bound_common.cuh", "ivb_iv.cuh", "ivb_fp64x.cuh"),
+    "specialised": ("ivb_jit.cpp", "ivb_bound_common.cuh", "ivb_iv.cuh", "ivb_fp64x.cuh"),
+}
+
+
+def kernel_sha(which):
     import hashlib
-    path = os.path.join(ROOT, "profiles", "k_bound_traffic.json")
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[which]:
+        with open(os.path.join(ROOT, "paper_2507_20769_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def traffic_for(subs_step, which):
+    """DRAM bytes per launch of the bounding kernel from the committed ncu
+    summary, scaled by subdomains, while the kernel's sources are the ones
+    that were profiled; None otherwise"""
+    path = os.path.join(ROOT, "profiles", "bound_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
-        rec = json.load(fh)
-    h = hashlib.sha256()
-    for name in ("ivb_kernels.cu", "ivb_iv.cuh", "ivb_fp64x.cuh"):
-        with open(os.path.join(ROOT, "paper_2507_20769_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
-    if rec.get("kernel_sha256") != h.hexdigest():
+        rec = json.load(fh).get(which)
+    if not rec or rec.get("kernel_sha256") != kernel_sha(which):
         return None
     return rec["dram_bytes_per_subdomain"] * subs_step
 

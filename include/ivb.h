@@ -104,6 +104,16 @@ typedef struct {
     int32_t tile;              /* subdomains a block grabs at a time; 0 = auto */
     int32_t max_nodes;         /* capacity of one call (default 4096)       */
     int32_t frame_in_shared;   /* -1 auto (default), 0 global, 1 shared     */
+    int32_t specialize;        /* 1: at creation, write the tape's programs
+                                  out as a straight-line CUDA kernel, compile
+                                  it with NVRTC for sm_103a and use it for
+                                  ivb_bound_nodes / _ex (bit-identical bounds,
+                                  values in registers instead of frame memory;
+                                  creation fails with IVB_ENOTSUP if it cannot
+                                  be compiled); 0 (default): tape interpreter;
+                                  -1: specialise when the tape is small enough
+                                  for a short compile (at most 4096 interval
+                                  operations per subdomain), else interpret  */
 } ivb_options;
 
 typedef struct ivb_problem ivb_problem;
@@ -244,6 +254,21 @@ ivb_status ivb_bnb_solve(ivb_problem* p, int32_t n, const double* root, const iv
  * block threads, blocks per SM, tile, frame in shared (0/1). */
 ivb_status ivb_get_tuning(ivb_problem* p, int32_t* block_threads, int32_t* blocks_per_sm,
                           int32_t* tile, int32_t* frame_in_shared);
+
+/* The tape-specialised kernel of a problem (may be NULL): active (0/1),
+ * registers per thread, local memory bytes per thread, NVRTC compile time in
+ * seconds. Not part of the paper's method: reports how the bounds are
+ * computed, not what they are. */
+ivb_status ivb_get_specialization(ivb_problem* p, int32_t* active, int32_t* registers,
+                                  int32_t* local_bytes, double* compile_seconds);
+
+/* Generate and compile (NVRTC, sm_103a) the tape-specialised kernel of a
+ * tape without loading it -- needs no GPU. Reports ptxas' registers per
+ * thread and spill-store bytes, and the compile time (each may be NULL).
+ * IVB_ETAPE for an invalid tape, IVB_ENOTSUP (message in ivb_last_error(NULL))
+ * when the program does not compile. */
+ivb_status ivb_specialize_compile(const ivb_tape* tape, int32_t grad_mode, int32_t* registers,
+                                  int32_t* spill_bytes, double* compile_seconds);
 
 /* Static count of the outward-rounded endpoint operations one subdomain
  * needs under the problem's gradient mode (the canonical formulas: value,

@@ -165,15 +165,27 @@ size_t smem_bytes(const ivb_problem* p, int block, int frame_smem) {
     return frame_smem ? (size_t)block * frame_units(p) * sizeof(double) : 0;
 }
 
+bool use_jit(const ivb_problem* p) { return p->jit.kern != nullptr; }
+
+// the reduce-mode bounding kernel: tape-specialised when compiled, else the interpreter
+cudaError_t launch_reduce(ivb_problem* p, const KParams& K, int grid, int block, int frame_smem, cudaStream_t s) {
+    if (use_jit(p)) return jit_launch(p->jit, K, grid, block, s);
+    return launch_bound(kernel_mode(p, false), K, grid, block, smem_bytes(p, block, frame_smem), s);
+}
+
+// resident blocks per SM of the reduce kernel
+int reduce_occupancy(ivb_problem* p, int block, int frame_smem) {
+    if (use_jit(p)) return block <= p->jit.max_threads ? jit_occupancy(p->jit, block) : 0;
+    return occupancy_blocks(kernel_mode(p, false), block, smem_bytes(p, block, frame_smem));
+}
+
 // enqueue: keys, counter, bound kernel, finalize (the batched graph body)
 ivb_status enqueue_bound(ivb_problem* p, int grid, int block, int tile, int frame_smem, int max_nodes, cudaStream_t s) {
-    const int mode = kernel_mode(p, false);
     CK(launch_init_keys(p->d_keys, p->d_queue, max_nodes, p->n_out, s));
     CK(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned long long), s));
     KParams K = make_params(p, frame_smem);
     K.tile = tile;
-    const size_t sm = smem_bytes(p, block, frame_smem);
-    CK(launch_bound(mode, K, grid, block, sm, s));
+    CK(launch_reduce(p, K, grid, block, frame_smem, s));
     FinalizeParams F{};
     F.keys = p->d_keys;
     F.queue = p->d_queue;
@@ -201,10 +213,9 @@ struct TuneCand {
 // the choice). The timed index range is capped at a few waves of the widest
 // candidate grid so that tuning stays a small fraction of one call.
 ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
-    const int mode = kernel_mode(p, false);
     std::vector<TuneCand> cands;
     const int blocks[] = {64, 128, 256};
-    const int bpss[] = {1, 2, 4, 8};
+    const int bpss[] = {1, 2, 3, 4, 6, 8};
     int max_threads = 0;
     for (int b : blocks)
         for (int k : bpss) {
@@ -212,10 +223,10 @@ ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
             if (warps < 4 || warps > 32) continue;
             for (int sm = 0; sm < 2; ++sm) {
                 const size_t bytes = smem_bytes(p, b, sm);
-                if (sm && (bytes + 1024 > (size_t)p->smem_optin || bytes * k > 220 * 1024)) continue;
+                if (sm && (use_jit(p) || bytes + 1024 > (size_t)p->smem_optin || bytes * k > 220 * 1024)) continue;
                 if (p->opt.frame_in_shared == 0 && sm) continue;
-                if (p->opt.frame_in_shared == 1 && !sm) continue;
-                if (occupancy_blocks(mode, b, bytes) < k) continue;
+                if (p->opt.frame_in_shared == 1 && !sm && !use_jit(p)) continue;
+                if (reduce_occupancy(p, b, sm) < k) continue;
                 cands.push_back({b, k, sm});
                 max_threads = std::max(max_threads, b * k * p->sm_count);
             }
@@ -236,7 +247,7 @@ ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
     ivb_status st = IVB_OK;
     for (const TuneCand& c : cands) {
         const int grid = p->sm_count * c.bps;
-        st = ensure_frame(p, grid, c.block);
+        if (!use_jit(p)) st = ensure_frame(p, grid, c.block);
         if (st) break;
         const int tile = c.block * 4;
         for (int rep = 0; rep < 2 && !st; ++rep) {      // warm-up, then timed
@@ -268,14 +279,14 @@ ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
 }
 
 ivb_status default_tuning(ivb_problem* p) {
-    const int mode = kernel_mode(p, false);
     p->block = p->opt.block_threads > 0 ? p->opt.block_threads : 128;
     p->bps = p->opt.blocks_per_sm > 0 ? p->opt.blocks_per_sm : 4;
     const size_t bytes = smem_bytes(p, p->block, 1);
-    if (p->opt.frame_in_shared == 1) p->frame_smem = 1;
+    if (use_jit(p)) p->frame_smem = 0;   // frames serve only the interpreter's store mode
+    else if (p->opt.frame_in_shared == 1) p->frame_smem = 1;
     else if (p->opt.frame_in_shared == 0) p->frame_smem = 0;
     else p->frame_smem = (bytes + 1024 <= (size_t)p->smem_optin && bytes * p->bps <= 220 * 1024) ? 1 : 0;
-    const int occ = occupancy_blocks(mode, p->block, smem_bytes(p, p->block, p->frame_smem));
+    const int occ = reduce_occupancy(p, p->block, p->frame_smem);
     if (occ < 1) return fail(p, IVB_ENOTSUP, "launch configuration does not fit on an SM");
     if (p->bps > occ) p->bps = occ;
     p->tile = p->opt.tile > 0 ? ((p->opt.tile + p->block - 1) / p->block) * p->block : p->block * 4;
@@ -309,6 +320,23 @@ ivb_status deliver(ivb_problem* p, int n_nodes, double* out_lb, uint8_t* out_inf
 
 // ======================================================================= ABI
 
+// generate, compile and load the tape-specialised reduce kernel
+cudaError_t specialize(ivb_problem* p, const std::vector<Ins>& ins, const std::vector<RIns>& rins,
+                       const std::vector<double>& consts, int mode, std::string* msg) {
+    const std::string src = jit_source(p->P, ins, rins, consts, mode, kJitBlockMax, kJitMinBlocks);
+    std::vector<char> cubin;
+    std::string tables;
+    double secs = 0.0;
+    *msg = jit_compile(src, cubin, tables, &secs, nullptr, nullptr);
+    if (!msg->empty()) return cudaSuccess;
+    const cudaError_t ce = jit_load(cubin, tables, p->jit);
+    if (ce != cudaSuccess) return ce;
+    p->jit.mode = mode;
+    p->jit.block_max = kJitBlockMax;
+    p->jit.compile_seconds = secs;
+    return cudaSuccess;
+}
+
 extern "C" void ivb_options_default(ivb_options* o) {
     if (!o) return;
     o->grad_mode = IVB_GRAD_ADJOINT;
@@ -322,6 +350,7 @@ extern "C" void ivb_options_default(ivb_options* o) {
     o->tile = 0;
     o->max_nodes = 4096;
     o->frame_in_shared = -1;
+    o->specialize = 0;
 }
 
 extern "C" ivb_status ivb_create_problem(const ivb_tape* tape, const ivb_options* opt, ivb_problem** out) {
@@ -338,6 +367,9 @@ extern "C" ivb_status ivb_create_problem(const ivb_tape* tape, const ivb_options
     if (o.max_nodes < 1 || o.max_nodes > (1 << 20)) return fail(nullptr, IVB_EINVAL, "max_nodes must be in [1, 2^20]");
     if (o.block_threads < 0 || o.block_threads > 512 || (o.block_threads % 32))
         return fail(nullptr, IVB_EINVAL, "block_threads must be a multiple of 32 up to 512 (0 = auto)");
+    if (o.specialize < -1 || o.specialize > 1) return fail(nullptr, IVB_EINVAL, "specialize must be -1, 0 or 1");
+    if (o.specialize && o.block_threads > kJitBlockMax)
+        return fail(nullptr, IVB_EINVAL, "block_threads above 256 with a tape-specialised kernel");
     ivb_problem* p = new ivb_problem();
     p->opt = o;
     std::vector<Ins> ins;
@@ -415,6 +447,27 @@ extern "C" ivb_status ivb_create_problem(const ivb_tape* tape, const ivb_options
     CKC(cudaMalloc(&p->d_minlo, (size_t)p->max_nodes * p->n_out * sizeof(double)));
     CKC(cudaMalloc(&p->d_maxhi, (size_t)p->max_nodes * p->n_out * sizeof(double)));
     CKC(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    if (o.specialize) {
+        const int64_t* cnt = o.grad_mode == IVB_GRAD_ADJOINT ? p->P.cnt_adj : p->P.cnt_fwd;
+        long long ops = 0;
+        for (int k = 0; k < IVB_CNT_N; ++k) ops += cnt[k];
+        if (o.specialize == 1 || ops / 2 <= kJitAutoMaxOps) {
+            const int mode = o.grad_mode == IVB_GRAD_ADJOINT ? KM_ADJ_REDUCE : KM_FWD_REDUCE;
+            std::string msg;
+            const cudaError_t ce = specialize(p, ins, rins, consts, mode, &msg);
+            if (ce != cudaSuccess || !msg.empty()) {
+                jit_unload(p->jit);
+                if (o.specialize == 1) {
+                    ivb_destroy(p);
+                    if (ce != cudaSuccess)
+                        return fail(nullptr, ce == cudaErrorMemoryAllocation ? IVB_ENOMEM : IVB_ECUDA,
+                                    std::string("loading the tape-specialised kernel: ") + cudaGetErrorString(ce));
+                    return fail(nullptr, IVB_ENOTSUP, msg);
+                }
+                cudaGetLastError();
+            }
+        }
+    }
 #undef CKC
     *out = p;
     return IVB_OK;
@@ -456,14 +509,13 @@ extern "C" ivb_status ivb_bound_nodes_ex(ivb_problem* p, int32_t n_nodes, const 
             const long long S = o2[1];
             const long long tiles = (S + p->block - 1) / p->block;
             const int grid = (int)std::min<long long>(tiles, (long long)p->sm_count * p->bps);
-            st = ensure_frame(p, grid, p->block);
+            if (!use_jit(p)) st = ensure_frame(p, grid, p->block);
             if (st) return st;
-            const int mode = kernel_mode(p, false);
             CK(launch_init_keys(p->d_keys, p->d_queue, 1, p->n_out, s));
             CK(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned long long), s));
             KParams K = make_params(p, p->frame_smem);
             K.tile = p->block;
-            CK(launch_bound(mode, K, grid, p->block, smem_bytes(p, p->block, p->frame_smem), s));
+            CK(launch_reduce(p, K, grid, p->block, p->frame_smem, s));
             FinalizeParams F{};
             F.keys = p->d_keys; F.queue = p->d_queue; F.max_nodes = 1; F.n_out = p->n_out; F.obj = p->obj;
             F.filter = p->opt.filter; F.out_kind = p->d_out_kind;
@@ -486,7 +538,7 @@ extern "C" ivb_status ivb_bound_nodes_ex(ivb_problem* p, int32_t n_nodes, const 
             if (st) return st;
         }
         const int grid = p->sm_count * p->bps;
-        st = ensure_frame(p, grid, p->block);
+        if (!use_jit(p)) st = ensure_frame(p, grid, p->block);
         if (st) return st;
         if (p->opt.use_graph) {
             if (!p->gexec) {
@@ -671,6 +723,40 @@ extern "C" ivb_status ivb_get_tuning(ivb_problem* p, int32_t* block_threads, int
     return IVB_OK;
 }
 
+extern "C" ivb_status ivb_get_specialization(ivb_problem* p, int32_t* active, int32_t* registers,
+                                             int32_t* local_bytes, double* compile_seconds) {
+    if (!p) return fail(nullptr, IVB_EINVAL, "problem handle is NULL");
+    if (active) *active = use_jit(p) ? 1 : 0;
+    if (registers) *registers = p->jit.regs;
+    if (local_bytes) *local_bytes = p->jit.local_bytes;
+    if (compile_seconds) *compile_seconds = p->jit.compile_seconds;
+    return IVB_OK;
+}
+
+extern "C" ivb_status ivb_specialize_compile(const ivb_tape* tape, int32_t grad_mode, int32_t* registers,
+                                             int32_t* spill_bytes, double* seconds) {
+    std::string e = validate_tape(tape);
+    if (!e.empty()) return fail(nullptr, IVB_ETAPE, e);
+    if (grad_mode != IVB_GRAD_FORWARD && grad_mode != IVB_GRAD_ADJOINT)
+        return fail(nullptr, IVB_EINVAL, "grad_mode must be IVB_GRAD_FORWARD or IVB_GRAD_ADJOINT");
+    HostProgram P;
+    std::vector<Ins> ins;
+    std::vector<RIns> rins;
+    std::vector<double> consts;
+    e = compile_tape(tape, P, ins, rins, consts);
+    if (!e.empty()) return fail(nullptr, IVB_ENOTSUP, e);
+    const int mode = grad_mode == IVB_GRAD_ADJOINT ? KM_ADJ_REDUCE : KM_FWD_REDUCE;
+    const std::string src = jit_source(P, ins, rins, consts, mode, kJitBlockMax, kJitMinBlocks);
+    std::vector<char> cubin;
+    std::string tables;
+    int regs = 0, spill = 0;
+    e = jit_compile(src, cubin, tables, seconds, &regs, &spill);
+    if (!e.empty()) return fail(nullptr, IVB_ENOTSUP, e);
+    if (registers) *registers = regs;
+    if (spill_bytes) *spill_bytes = spill;
+    return IVB_OK;
+}
+
 extern "C" ivb_status ivb_eval_op(int32_t opcode, int64_t n, const double* x, const double* y, double* r,
                                   void* cuda_stream) {
     if (n < 0 || !x || !r) return fail(nullptr, IVB_EINVAL, "ivb_eval_op: x and r are required");
@@ -720,5 +806,6 @@ extern "C" void ivb_destroy(ivb_problem* p) {
     cudaFree(p->d_maxhi);
     cudaFree(p->d_frame);
     cudaFree(p->d_pframe);
+    jit_unload(p->jit);
     delete p;
 }

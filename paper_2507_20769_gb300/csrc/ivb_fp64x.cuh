@@ -21,11 +21,14 @@
 // widening below 1.5 ulp of the result; the interval ends are then moved two
 // neighbour steps outward, which encloses the true value.
 #pragma once
+#ifndef __CUDACC_RTC__
 #include <cstdint>
+#endif
 
 namespace ivb {
 
-// tables, in device memory of this module (filled by init_math_tables)
+// tables, in device memory of this module (filled by init_math_tables, or
+// copied from the library's tables into a tape-specialised module)
 constexpr int kExpTab = 512, kLogTab = 2048;
 struct ExpEntry { double hi, lo; };            // 2^(j/512) as hi + lo
 struct LogEntry { double c, hi, lo, pad; };    // reciprocal centre c_j, -log(c_j) as hi + lo
@@ -33,7 +36,11 @@ struct MathTables {
     ExpEntry exp[kExpTab];
     LogEntry log[kLogTab];
 };
+#ifdef __CUDACC_RTC__
+__device__ MathTables g_math;          // run-time compiled module: filled from the library's copy
+#else
 static __device__ MathTables g_math;
+#endif
 
 __device__ __forceinline__ float rcp_approx_f(float x) {
     float r;

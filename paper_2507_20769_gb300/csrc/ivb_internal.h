@@ -13,7 +13,9 @@
 // Operands name a slot (per-thread frame record), a variable of the box or
 // an entry of the constant table, so VAR and CONST entries cost no storage.
 #pragma once
+#ifndef __CUDACC_RTC__
 #include <cstdint>
+#endif
 
 namespace ivb {
 

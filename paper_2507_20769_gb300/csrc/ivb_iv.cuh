@@ -14,7 +14,9 @@
 // product costs two directed multiplies (four only when both factors contain
 // zero in their interior).
 #pragma once
+#ifndef __CUDACC_RTC__
 #include <cstdint>
+#endif
 
 namespace ivb {
 

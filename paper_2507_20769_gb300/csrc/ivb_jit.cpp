@@ -1,0 +1,444 @@
+// ivb_jit.cpp -- tape-specialised bounding kernels.
+//
+// The tape interpreter (ivb_kernels.cu) fetches, decodes and dispatches every
+// instruction at run time and keeps every interval in per-thread frame memory.
+// At problem creation, when asked to, this file writes the very programs the
+// interpreter runs (the point sweep on [c,c], then per output either the
+// tangent sweep or the forward sweep plus reverse adjoint sweep of Section
+// 3.2) out as straight-line CUDA C++ -- one statement per instruction, frame
+// records turned into named local variables -- around the shared tile loop,
+// decoding, Mean Value Form sum and reductions of ivb_bound_common.cuh,
+// compiles it with NVRTC for sm_103a and loads it as a CUDA library.
+//
+// Every statement calls the same interval primitive on the same operands as
+// the interpreter does, in the same order wherever the order changes a
+// rounded result (adjoint accumulation, the MVF sum), so the bounds are
+// bit-identical to the interpreter's. What changes: no instruction stream,
+// operands in registers, and the compiler is free to interleave independent
+// operations, which hides the latency of the narrow FP64 pipe.
+#include <cuda_runtime.h>
+#include <nvrtc.h>
+
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ivb.h"
+#include "ivb_internal.h"
+#include "ivb_jit.h"
+#include "ivb_kernels.h"
+
+// device headers as strings (written by the build from csrc/)
+#include "ivb_jit_headers.inc"
+
+namespace ivb {
+
+namespace {
+
+// exact hexadecimal literal of a finite double
+std::string lit(double v) {
+    char buf[64];
+    std::snprintf(buf, sizeof buf, "%a", v);
+    return std::string("(") + buf + ")";
+}
+
+std::string S(long long v) { return std::to_string(v); }
+
+struct Gen {
+    const HostProgram& P;
+    const Ins* ins;
+    const RIns* rins;
+    const double* consts;
+    int n, no;
+    std::string out;
+
+    void line(int ind, const std::string& s) {
+        out.append((size_t)ind * 2, ' ');
+        out += s;
+        out += '\n';
+    }
+
+    std::string konst(uint32_t idx) const { return "mk(" + lit(consts[idx]) + ", " + lit(consts[idx]) + ")"; }
+
+    // value operand: role 'p' point sweep (variables read [c,c]), 't' tangent
+    // records, 'r' adjoint tape records (variables read X)
+    std::string val(char role, uint32_t kind, uint32_t idx) const {
+        if (kind == K_SLOT) return std::string(1, role) + S(idx);
+        if (kind == K_VAR) return role == 'p' ? "mk(c" + S(idx) + ", c" + S(idx) + ")" : "X" + S(idx);
+        return konst(idx);
+    }
+
+    static std::string eval(uint32_t op, const std::string& A, const std::string& B) {
+        switch (op) {
+        case OP_ADD: return "iv_add(" + A + ", " + B + ")";
+        case OP_SUB: return "iv_sub(" + A + ", " + B + ")";
+        case OP_MUL: return "iv_mul(" + A + ", " + B + ")";
+        case OP_DIV: return "iv_div(" + A + ", " + B + ")";
+        case OP_SQR: return "iv_sqr(" + A + ")";
+        case OP_SQRT: return "iv_sqrt(" + A + ")";
+        case OP_EXP: return "iv_exp(" + A + ")";
+        case OP_LOG: return "iv_log(" + A + ")";
+        case OP_NEG: return "iv_neg(" + A + ")";
+        }
+        return "entire()";
+    }
+
+    void decls(int ind, const char* prefix, int count) {
+        for (int i = 0; i < count; i += 8) {
+            std::string s = "iv ";
+            for (int j = i; j < count && j < i + 8; ++j) s += (j > i ? ", " : "") + std::string(prefix) + S(j) + " = zero()";
+            line(ind, s + ";");
+        }
+    }
+
+    // straight-line value sweep (run_values): dst record of each instruction
+    void values(int ind, char role, int begin, int count) {
+        for (int i = begin; i < begin + count; ++i) {
+            const Ins I = ins[i];
+            const uint32_t op = I.w0 & 31u, ak = (I.w0 >> 5) & 3u, bk = (I.w0 >> 7) & 3u, dst = I.w0 >> 16;
+            const std::string A = val(role, ak, I.w1 & 0xFFFFu);
+            const std::string B = bk != K_NONE ? val(role, bk, I.w1 >> 16) : A;
+            line(ind, std::string(1, role) + S(dst) + " = " + eval(op, A, B) + ";");
+        }
+    }
+
+    // tangent of an operand in direction d (load_tan)
+    std::string tan(uint32_t kind, uint32_t idx, int d) const {
+        if (kind == K_SLOT) return "t" + S(idx) + "_" + S(d);
+        if (kind == K_VAR) return (int)idx == d ? "one()" : "zero()";
+        return "zero()";
+    }
+
+    // forward-mode sweep (run_tangents), records t<k> and t<k>_<d>
+    void tangents(int ind) {
+        for (int i = P.tan_begin; i < P.tan_begin + P.tan_count; ++i) {
+            const Ins I = ins[i];
+            const uint32_t op = I.w0 & 31u, ak = (I.w0 >> 5) & 3u, bk = (I.w0 >> 7) & 3u, dst = I.w0 >> 16;
+            const uint32_t ai = I.w1 & 0xFFFFu, bi = I.w1 >> 16;
+            const bool az = ak == K_CONST, bz = bk == K_CONST || bk == K_NONE;
+            line(ind, "{");
+            const int j = ind + 1;
+            line(j, "const iv A = " + val('t', ak, ai) + ";");
+            line(j, std::string("const iv B = ") + (bk != K_NONE ? val('t', bk, bi) : "A") + ";");
+            line(j, "const iv V = " + eval(op, "A", "B") + ";");
+            const std::string T = "t" + S(dst) + "_";
+            switch (op) {
+            case OP_ADD:
+                for (int d = 0; d < n; ++d)
+                    line(j, T + S(d) + " = " +
+                                (az ? tan(bk, bi, d) : bz ? tan(ak, ai, d)
+                                                          : "iv_add(" + tan(ak, ai, d) + ", " + tan(bk, bi, d) + ")") + ";");
+                break;
+            case OP_SUB:
+                for (int d = 0; d < n; ++d)
+                    line(j, T + S(d) + " = " +
+                                (az ? "iv_neg(" + tan(bk, bi, d) + ")"
+                                    : bz ? tan(ak, ai, d) : "iv_sub(" + tan(ak, ai, d) + ", " + tan(bk, bi, d) + ")") + ";");
+                break;
+            case OP_NEG:
+                for (int d = 0; d < n; ++d) line(j, T + S(d) + " = iv_neg(" + tan(ak, ai, d) + ");");
+                break;
+            case OP_MUL:
+                for (int d = 0; d < n; ++d) {
+                    std::string t;
+                    if (az) t = "iv_mul(A, " + tan(bk, bi, d) + ")";
+                    else if (bz) t = "iv_mul(" + tan(ak, ai, d) + ", B)";
+                    else t = "iv_add(iv_mul(" + tan(ak, ai, d) + ", B), iv_mul(A, " + tan(bk, bi, d) + "))";
+                    line(j, T + S(d) + " = " + t + ";");
+                }
+                break;
+            case OP_DIV:
+                line(j, "const iv R = iv_recip(B);");
+                for (int d = 0; d < n; ++d) {
+                    std::string t;
+                    if (bz) t = "iv_mul(" + tan(ak, ai, d) + ", R)";
+                    else if (az) t = "iv_mul(iv_neg(iv_mul(V, " + tan(bk, bi, d) + ")), R)";
+                    else t = "iv_mul(iv_sub(" + tan(ak, ai, d) + ", iv_mul(V, " + tan(bk, bi, d) + ")), R)";
+                    line(j, T + S(d) + " = " + t + ";");
+                }
+                break;
+            case OP_SQR:
+                line(j, "const iv D = iv_twice(A);");
+                for (int d = 0; d < n; ++d) line(j, T + S(d) + " = iv_mul(D, " + tan(ak, ai, d) + ");");
+                break;
+            case OP_SQRT:
+                line(j, "const iv R = iv_recip_pos(iv_twice(V));");
+                for (int d = 0; d < n; ++d) line(j, T + S(d) + " = iv_mul(" + tan(ak, ai, d) + ", R);");
+                break;
+            case OP_EXP:
+                for (int d = 0; d < n; ++d) line(j, T + S(d) + " = iv_mul(V, " + tan(ak, ai, d) + ");");
+                break;
+            case OP_LOG:
+                line(j, "const iv R = iv_recip_pos(A);");
+                for (int d = 0; d < n; ++d) line(j, T + S(d) + " = iv_mul(" + tan(ak, ai, d) + ", R);");
+                break;
+            }
+            line(j, "t" + S(dst) + " = V;");
+            line(ind, "}");
+        }
+    }
+
+    // reverse sweep of one output (run_reverse): adjoint slots w<k>, tape
+    // records r<k>, gradient accumulators g<i>
+    void reverse(int ind, const AdjProgram& A) {
+        for (int i = A.rv_begin; i < A.rv_begin + A.rv_count; ++i) {
+            const RIns R = rins[i];
+            const uint32_t op = R.w0 & 31u, wslot = R.w0 >> 16;
+            const std::string W = "w" + S(wslot);
+            if (op == OP_VAR) {
+                const std::string g = "g" + S(R.w1);
+                line(ind, g + " = iv_add(" + g + ", " + W + ");");
+                continue;
+            }
+            const bool a_init = (R.w0 >> 5) & 1u, b_init = (R.w0 >> 6) & 1u;
+            const bool a_none = (R.w0 >> 7) & 1u, b_none = (R.w0 >> 8) & 1u;
+            const uint32_t Ak = (R.w3 >> 16) & 3u, Bk = (R.w3 >> 18) & 3u;
+            const std::string Av = val('r', Ak, R.w2 & 0xFFFFu), Bv = val('r', Bk, R.w2 >> 16);
+            const std::string V = "r" + S(R.w3 & 0xFFFFu);
+            std::string ca, cb;
+            bool sub_a = false, sub_b = false;
+            line(ind, "{");
+            const int j = ind + 1;
+            line(j, "const iv W = " + W + ";");
+            switch (op) {
+            case OP_ADD: ca = "W"; cb = "W"; break;
+            case OP_SUB: ca = "W"; cb = "W"; sub_b = true; break;
+            case OP_NEG: ca = "W"; sub_a = true; break;
+            case OP_MUL:
+                if (!a_none) ca = "iv_mul(W, " + Bv + ")";
+                if (!b_none) cb = "iv_mul(W, " + Av + ")";
+                break;
+            case OP_DIV:
+                line(j, "const iv Rb = iv_recip(" + Bv + ");");
+                if (!a_none) ca = "iv_mul(W, Rb)";
+                if (!b_none) cb = "iv_mul(iv_mul(W, " + V + "), Rb)";
+                sub_b = true;
+                break;
+            case OP_SQR: ca = "iv_mul(W, iv_twice(" + Av + "))"; break;
+            case OP_SQRT: ca = "iv_mul(W, iv_recip_pos(iv_twice(" + V + ")))"; break;
+            case OP_EXP: ca = "iv_mul(W, " + V + ")"; break;
+            case OP_LOG: ca = "iv_mul(W, iv_recip_pos(" + Av + "))"; break;
+            default: ca = "entire()"; cb = "entire()";
+            }
+            // both contributions are formed before either slot is written
+            if (!a_none) line(j, "const iv ca = " + ca + ";");
+            if (!b_none) line(j, "const iv cb = " + cb + ";");
+            if (!a_none) {
+                const std::string u = "w" + S(R.w1 & 0xFFFFu);
+                line(j, u + " = " + (a_init ? (sub_a ? "iv_neg(ca)" : "ca")
+                                            : (sub_a ? "iv_sub(" + u + ", ca)" : "iv_add(" + u + ", ca)")) + ";");
+            }
+            if (!b_none) {
+                const std::string u = "w" + S(R.w1 >> 16);
+                line(j, u + " = " + (b_init ? (sub_b ? "iv_neg(cb)" : "cb")
+                                            : (sub_b ? "iv_sub(" + u + ", cb)" : "iv_add(" + u + ", cb)")) + ";");
+            }
+            line(ind, "}");
+        }
+    }
+
+    // MVF, form and tests of output o (gradient expressions G_i, NIE expression)
+    void finish(int ind, int o, const std::vector<std::string>& Gi, const std::string& nie) {
+        line(ind, "{");
+        const int j = ind + 1;
+        line(j, "iv mvf = fc" + S(o) + ";");
+        for (int i = 0; i < n; ++i) line(j, "mvf = mvf_term(mvf, " + Gi[i] + ", X" + S(i) + ", c" + S(i) + ");");
+        line(j, "F" + S(o) + " = final_form(P.form, mvf, " + nie + ");");
+        line(j, "if (excludes_feasible(" + S(P.out_kind[o]) + "u, F" + S(o) + ")) cert = true;");
+        if (o == P.obj) line(j, "obj_lo = F" + S(o) + ".lo;");
+        line(ind, "}");
+    }
+
+    std::string kernel(int mode, int block_max, int min_blocks) {
+        out.clear();
+        line(0, "typedef signed char int8_t; typedef unsigned char uint8_t;");
+        line(0, "typedef short int16_t; typedef unsigned short uint16_t;");
+        line(0, "typedef int int32_t; typedef unsigned int uint32_t;");
+        line(0, "typedef long long int64_t; typedef unsigned long long uint64_t;");
+        line(0, "#include \"ivb_bound_common.cuh\"");
+        line(0, "extern \"C\" __global__ void __launch_bounds__(" + S(block_max) + ", " + S(min_blocks) +
+                    ") ivb_jit_bound(const ivb::KParams P) {");
+        line(1, "using namespace ivb;");
+        line(1, "tile_loop(P, [&](const Sub& s) {");
+        int d = 2;
+        {
+            std::string f = "iv ";
+            for (int o = 0; o < no; ++o) f += (o ? ", F" : "F") + S(o) + " = zero()";
+            line(d, f + ";");
+        }
+        line(d, "bool cert = false;");
+        line(d, "double obj_lo = from_bits(0x7FF0000000000000LL);");
+        line(d, "double ub = from_bits(0x7FF0000000000000LL);");
+        line(d, "if (s.valid) {");
+        d = 3;
+        // Step 1
+        decls(d, "X", n);
+        for (int i = 0; i < n; ++i) line(d, "double c" + S(i) + " = 0.0;");
+        line(d, "unsigned int kk = s.k;");
+        for (int i = 0; i < n; ++i) line(d, "decode_dim(s.rec, " + S(n) + ", " + S(i) + ", kk, X" + S(i) + ", c" + S(i) + ");");
+        // Step 2a: point sweep
+        decls(d, "fc", no);
+        line(d, "{");
+        decls(d + 1, "p", P.pt_slots);
+        values(d + 1, 'p', P.pt_begin, P.pt_count);
+        for (int o = 0; o < no; ++o)
+            line(d + 1, "fc" + S(o) + " = " + val('p', (uint32_t)P.pt_out_kind[o], (uint32_t)P.pt_out_ref[o]) + ";");
+        line(d, "}");
+        // Step 2b
+        if (mode == KM_FWD_REDUCE) {
+            line(d, "{");
+            const int e = d + 1;
+            for (int k = 0; k < P.tan_slots; ++k) {
+                line(e, "iv t" + S(k) + " = zero();");
+                decls(e, ("t" + S(k) + "_").c_str(), n);
+            }
+            tangents(e);
+            for (int o = 0; o < no; ++o) {
+                const uint32_t kind = (uint32_t)P.tan_out_kind[o], ref = (uint32_t)P.tan_out_ref[o];
+                std::vector<std::string> G(n);
+                for (int i = 0; i < n; ++i)
+                    G[i] = kind == K_SLOT ? "t" + S(ref) + "_" + S(i)
+                                          : (kind == K_VAR && (int)ref == i) ? "one()" : "zero()";
+                finish(e, o, G, val('t', kind, ref));
+            }
+            line(d, "}");
+        } else {
+            for (int o = 0; o < no; ++o) {
+                const AdjProgram& A = P.adj[o];
+                line(d, "{  // output " + S(o) + ": forward sweep over its cone, then the reverse sweep");
+                const int e = d + 1;
+                decls(e, "r", A.tape_records);
+                decls(e, "w", A.adj_slots);
+                decls(e, "g", n);
+                values(e, 'r', A.fw_begin, A.fw_count);
+                if (A.out_wslot >= 0) line(e, "w" + S(A.out_wslot) + " = one();");
+                reverse(e, A);
+                std::vector<std::string> G(n);
+                for (int i = 0; i < n; ++i) G[i] = "g" + S(i);
+                finish(e, o, G, val('r', (uint32_t)A.out_kind_ref, (uint32_t)A.out_ref));
+                line(d, "}");
+            }
+        }
+        // certified-feasible centre upper bound; filtered objective
+        line(d, std::string("bool feas = ") + (P.has_eq ? "false" : "true") + ";");
+        for (int o = 0; o < no; ++o)
+            if (P.out_kind[o] == OUT_INEQ) line(d, "if (!le0(fc" + S(o) + ".hi)) feas = false;");
+        line(d, "if (feas) ub = fc" + S(P.obj) + ".hi;");
+        line(d, "if (cert) obj_lo = from_bits(0x7FF0000000000000LL);");
+        line(2, "}");
+        for (int o = 0; o < no; ++o) line(2, "reduce_output(P, s, " + S(no) + ", " + S(o) + ", F" + S(o) + ");");
+        line(2, "reduce_extras(P, s, " + S(no) + ", ub, obj_lo);");
+        line(1, "});");
+        line(0, "}");
+        return out;
+    }
+};
+
+}  // namespace
+
+std::string jit_source(const HostProgram& P, const std::vector<Ins>& ins, const std::vector<RIns>& rins,
+                       const std::vector<double>& consts, int mode, int block_max, int min_blocks) {
+    Gen g{P, ins.data(), rins.data(), consts.data(), P.n_vars, P.n_out, {}};
+    return g.kernel(mode, block_max, min_blocks);
+}
+
+std::string jit_compile(const std::string& src, std::vector<char>& cubin, std::string& tables_name, double* seconds,
+                        int* registers, int* spill_bytes) {
+    const auto t0 = std::chrono::steady_clock::now();
+    nvrtcProgram prog;
+    const int nh = (int)(sizeof(kJitHeaderNames) / sizeof(kJitHeaderNames[0]));
+    nvrtcResult r = nvrtcCreateProgram(&prog, src.c_str(), "ivb_jit_bound.cu", nh, kJitHeaderSources, kJitHeaderNames);
+    if (r != NVRTC_SUCCESS) return std::string("nvrtcCreateProgram: ") + nvrtcGetErrorString(r);
+    nvrtcAddNameExpression(prog, "&ivb::g_math");
+    const bool verbose = registers || spill_bytes;
+    const char* opts[] = {"-arch=sm_103a", "--fmad=false", "-std=c++17", "-lineinfo", "--ptxas-options=-v"};
+    r = nvrtcCompileProgram(prog, verbose ? 5 : 4, opts);
+    size_t ls = 0;
+    nvrtcGetProgramLogSize(prog, &ls);
+    std::string log(ls, '\0');
+    if (ls) nvrtcGetProgramLog(prog, &log[0]);
+    std::string err;
+    if (r != NVRTC_SUCCESS) {
+        err = std::string("NVRTC compilation of the tape-specialised kernel failed: ") + nvrtcGetErrorString(r) +
+              "\n" + log.substr(0, 4000);
+    } else {
+        // ptxas info lines: "Used N registers", "M bytes spill stores"
+        auto number_before = [&](const char* key) -> int {
+            const size_t at = log.find(key);
+            if (at == std::string::npos) return 0;
+            size_t b = at;
+            while (b > 0 && log[b - 1] == ' ') --b;
+            size_t e = b;
+            while (b > 0 && log[b - 1] >= '0' && log[b - 1] <= '9') --b;
+            return b < e ? std::atoi(log.substr(b, e - b).c_str()) : 0;
+        };
+        auto number_after = [&](const char* key) -> int {
+            const size_t at = log.find(key);
+            return at == std::string::npos ? -1 : std::atoi(log.c_str() + at + std::strlen(key));
+        };
+        if (registers) *registers = number_after("Used ");
+        if (spill_bytes) *spill_bytes = number_before(" bytes spill stores");
+        size_t cs = 0;
+        nvrtcGetCUBINSize(prog, &cs);
+        cubin.resize(cs);
+        nvrtcGetCUBIN(prog, cubin.data());
+        const char* low = nullptr;
+        nvrtcGetLoweredName(prog, "&ivb::g_math", &low);
+        tables_name = low ? low : "";
+        if (tables_name.empty()) err = "NVRTC: no lowered name for the math tables";
+    }
+    nvrtcDestroyProgram(&prog);
+    if (seconds) *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return err;
+}
+
+cudaError_t jit_load(const std::vector<char>& cubin, const std::string& tables_name, JitKernel& K) {
+    cudaError_t e = cudaLibraryLoadData(&K.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (e != cudaSuccess) return e;
+    e = cudaLibraryGetKernel(&K.kern, K.lib, "ivb_jit_bound");
+    if (e != cudaSuccess) return e;
+    // the module's own copy of the exp / log tables, from the library's
+    void* dst = nullptr;
+    size_t bytes = 0;
+    e = cudaLibraryGetGlobal(&dst, &bytes, K.lib, tables_name.c_str());
+    if (e != cudaSuccess) return e;
+    void* src = nullptr;
+    size_t sbytes = 0;
+    e = math_tables_address(&src, &sbytes);
+    if (e != cudaSuccess) return e;
+    if (bytes != sbytes) return cudaErrorInvalidValue;
+    e = cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes a{};
+    e = cudaFuncGetAttributes(&a, (const void*)K.kern);
+    if (e != cudaSuccess) return e;
+    K.regs = a.numRegs;
+    K.local_bytes = (int)a.localSizeBytes;
+    K.max_threads = a.maxThreadsPerBlock;
+    return cudaSuccess;
+}
+
+cudaError_t jit_launch(const JitKernel& K, const KParams& P, int grid, int block, cudaStream_t s) {
+    KParams p = P;
+    void* args[] = {&p};
+    return cudaLaunchKernel((const void*)K.kern, dim3(grid), dim3(block), args, 0, s);
+}
+
+int jit_occupancy(const JitKernel& K, int block) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)K.kern, block, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+void jit_unload(JitKernel& K) {
+    if (K.lib) cudaLibraryUnload(K.lib);
+    K = JitKernel{};
+}
+
+}  // namespace ivb

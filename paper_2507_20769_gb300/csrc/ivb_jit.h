@@ -1,0 +1,40 @@
+// ivb_jit.h -- tape-specialised bounding kernels (generated CUDA C++,
+// compiled with NVRTC at problem creation); see ivb_jit.cpp.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "ivb_internal.h"
+#include "ivb_kparams.h"
+
+namespace ivb {
+
+// generated kernels: __launch_bounds__(kJitBlockMax, kJitMinBlocks), i.e. at
+// most 128 registers per thread; specialize = -1 compiles tapes of at most
+// kJitAutoMaxOps interval operations per subdomain
+constexpr int kJitBlockMax = 256, kJitMinBlocks = 2, kJitAutoMaxOps = 4096;
+
+struct JitKernel {
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t kern = nullptr;
+    int mode = -1;             // KM_FWD_REDUCE or KM_ADJ_REDUCE
+    int block_max = 0;         // __launch_bounds__ of the generated kernel
+    int regs = 0, local_bytes = 0, max_threads = 0;
+    double compile_seconds = 0.0;
+};
+
+// CUDA C++ of the reduce-mode bounding kernel for this program
+std::string jit_source(const HostProgram& P, const std::vector<Ins>& ins, const std::vector<RIns>& rins,
+                       const std::vector<double>& consts, int mode, int block_max, int min_blocks);
+// NVRTC for sm_103a; "" on success, else the compiler's message. With
+// `registers` / `spill_bytes` non-NULL, ptxas reports them (parsed from its log).
+std::string jit_compile(const std::string& src, std::vector<char>& cubin, std::string& tables_name, double* seconds,
+                        int* registers, int* spill_bytes);
+cudaError_t jit_load(const std::vector<char>& cubin, const std::string& tables_name, JitKernel& K);
+cudaError_t jit_launch(const JitKernel& K, const KParams& P, int grid, int block, cudaStream_t s);
+int jit_occupancy(const JitKernel& K, int block);
+void jit_unload(JitKernel& K);
+
+}  // namespace ivb

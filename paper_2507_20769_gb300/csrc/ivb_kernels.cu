@@ -1,4 +1,5 @@
-// ivb_kernels.cu -- sm_103a kernels for Subdomain Lower Bounding (Section 3.1):
+// ivb_kernels.cu -- sm_103a kernels for Subdomain Lower Bounding (Section 3.1),
+// tape interpreter (tile loop, decoding and reductions in ivb_bound_common.cuh):
 //   Step 1: subdomain boxes decoded from the thread's global index (never
 //           stored), dimension 0 fastest (Section 3.1.1)
 //   Step 2: Mean Value Form (Definition 5) per subdomain: rigorous f(c) by an
@@ -13,6 +14,7 @@
 #include <cstdint>
 #include <cstring>
 
+#include "ivb_bound_common.cuh"
 #include "ivb_internal.h"
 #include "ivb_iv.cuh"
 #include "ivb_kernels.h"
@@ -224,54 +226,6 @@ __device__ void run_reverse(const RIns* __restrict__ rins, int count, const Swee
     }
 }
 
-// ------------------------------------------------------------ reduction keys
-// unsigned key with the order of the doubles (NaN maps to the given end)
-__device__ __forceinline__ unsigned long long ukey(double x) {
-    unsigned long long b = (unsigned long long)bits(x);
-    return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
-}
-__device__ __forceinline__ unsigned long long ukey_lo(double x) {   // NaN -> -inf
-    return isnan_(x) ? ukey(from_bits((long long)0xFFF0000000000000ULL)) : ukey(x);
-}
-__device__ __forceinline__ unsigned long long ukey_hi(double x) {   // NaN -> +inf
-    return isnan_(x) ? ukey(from_bits(0x7FF0000000000000LL)) : ukey(x);
-}
-__device__ __forceinline__ double unkey(unsigned long long k) {
-    return from_bits((long long)((k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFULL) : ~k));
-}
-
-__device__ __forceinline__ unsigned long long shfl_xor64(unsigned long long v, int m) {
-    unsigned lo = (unsigned)v, hi = (unsigned)(v >> 32);
-    lo = __shfl_xor_sync(0xFFFFFFFFu, lo, m);
-    hi = __shfl_xor_sync(0xFFFFFFFFu, hi, m);
-    return ((unsigned long long)hi << 32) | lo;
-}
-__device__ __forceinline__ unsigned long long warp_min64(unsigned long long v) {
-    for (int m = 16; m; m >>= 1) { unsigned long long o = shfl_xor64(v, m); v = o < v ? o : v; }
-    return v;
-}
-__device__ __forceinline__ unsigned long long warp_max64(unsigned long long v) {
-    for (int m = 16; m; m >>= 1) { unsigned long long o = shfl_xor64(v, m); v = o > v ? o : v; }
-    return v;
-}
-
-// min (is_min) or max of v into *dst: one atomic per warp when every lane of
-// the warp belongs to the same node, else one per lane; invalid lanes carry
-// the neutral key.
-__device__ __forceinline__ void reduce_key(unsigned long long* base, int node, int slot, int stride,
-                                           unsigned long long v, bool valid, bool uniform, bool is_min) {
-    if (uniform) {
-        unsigned long long r = is_min ? warp_min64(valid ? v : ~0ULL) : warp_max64(valid ? v : 0ULL);
-        if ((threadIdx.x & 31) == 0 && node >= 0) {
-            if (is_min) atomicMin(base + (size_t)node * stride + slot, r);
-            else atomicMax(base + (size_t)node * stride + slot, r);
-        }
-    } else if (valid) {
-        if (is_min) atomicMin(base + (size_t)node * stride + slot, v);
-        else atomicMax(base + (size_t)node * stride + slot, v);
-    }
-}
-
 // --------------------------------------------------------------- the kernel
 template <int MODE>
 __global__ void __launch_bounds__(512) k_bound(const KParams P) {
@@ -286,147 +240,99 @@ __global__ void __launch_bounds__(512) k_bound(const KParams P) {
     C.consts = G.consts;
     C.x_base = L.x_base;
     C.c_base = L.c_base;
-    const int K = 2 * n_out + 2;  // keys per node
 
-    // node queue: header, prefix offsets, records
-    const long long* qh = reinterpret_cast<const long long*>(P.queue);
-    const int n_nodes = (int)qh[0];
-    const long long total = qh[1];
-    const long long* off = reinterpret_cast<const long long*>(P.queue + kQueueHeader);
-    const char* recs = P.queue + kQueueHeader + 8 * (size_t)(n_nodes + 1);
-
-    __shared__ long long s_base;
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_base = (long long)atomicAdd(P.counter, (unsigned long long)P.tile);
-        __syncthreads();
-        const long long base = s_base;
-        if (base >= total) break;
-        const long long end = base + P.tile < total ? base + P.tile : total;
-        for (long long g0 = base; g0 < end; g0 += blockDim.x) {
-            const long long g = g0 + threadIdx.x;
-            const bool valid = g < end;
-            // node of g: largest node with off[node] <= g
-            int node = -1;
-            unsigned int k = 0;
+    tile_loop(P, [&](const Sub& s) {
+        const long long g = s.g;
+        const bool valid = s.valid;
+        if (valid) {
+            // ---- Step 1: decode X_k and c
+            unsigned int kk = s.k;
+            for (int i = 0; i < n; ++i) {
+                iv X;
+                double c;
+                decode_dim(s.rec, n, i, kk, X, c);
+                C.F.put(L.x_base + 2 * i, X);
+                C.F.st(L.c_base + i, c);
+            }
+            // ---- Step 2a: rigorous point value f(c) of every output
+            C.point = true;
+            run_values(G.ins + G.pt_begin, G.pt_count, C, L.phase_base);
+            for (int o = 0; o < n_out; ++o)
+                C.F.put(L.fc_base + 2 * o, load_val(C, G.pt_out_kind[o], G.pt_out_ref[o], L.phase_base, 2));
+            C.point = false;
+        }
+        // ---- Step 2b: gradient enclosures and the Mean Value Form, output by output
+        bool cert_infeasible = false;
+        double obj_lo = from_bits(0x7FF0000000000000LL);
+        if (MODE == KM_FWD_REDUCE || MODE == KM_FWD_STORE) {
+            if (valid) run_tangents(G.ins + G.tan_begin, G.tan_count, C, L.phase_base, n);
+        }
+        for (int o = 0; o < n_out; ++o) {
+            iv F = zero(), Fc = zero();
             if (valid) {
-                int lo = 0, hi = n_nodes - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (__ldg(off + mid) <= g) lo = mid; else hi = mid - 1;
-                }
-                node = lo;
-                k = (unsigned int)(g - __ldg(off + node));
-            }
-            const int node0 = __shfl_sync(0xFFFFFFFFu, node, 0);
-            const bool uniform = __all_sync(0xFFFFFFFFu, !valid || node == node0);
-            if (valid) {
-                // ---- Step 1: decode X_k and c (Section 2.2 splitting item i)
-                unsigned int kk = k;
-                const double* rlo = reinterpret_cast<const double*>(recs + (size_t)node * P.rec_bytes);
-                const int32_t* rN = reinterpret_cast<const int32_t*>(rlo + 3 * n);
-                for (int i = 0; i < n; ++i) {
-                    const unsigned int N = (unsigned int)__ldg(rN + i);
-                    const unsigned int j = kk % N;
-                    kk /= N;
-                    const double lo = __ldg(rlo + i), hi = __ldg(rlo + n + i), h = __ldg(rlo + 2 * n + i);
-                    double e0 = lo, e1 = hi;
-                    if (j > 0) e0 = imin(imax(__dadd_rn(lo, __dmul_rn((double)j, h)), lo), hi);
-                    if (j + 1 < N) e1 = imin(imax(__dadd_rn(lo, __dmul_rn((double)(j + 1), h)), lo), hi);
-                    C.F.put(L.x_base + 2 * i, mk(e0, e1));
-                    C.F.st(L.c_base + i, __dmul_rn(__dadd_rn(e0, e1), 0.5));
-                }
-                // ---- Step 2a: rigorous point value f(c) of every output
-                C.point = true;
-                run_values(G.ins + G.pt_begin, G.pt_count, C, L.phase_base);
-                for (int o = 0; o < n_out; ++o)
-                    C.F.put(L.fc_base + 2 * o, load_val(C, G.pt_out_kind[o], G.pt_out_ref[o], L.phase_base, 2));
-                C.point = false;
-            }
-            // ---- Step 2b: gradient enclosures and the Mean Value Form, output by output
-            bool cert_infeasible = false;
-            double obj_lo = from_bits(0x7FF0000000000000LL);
-            if (MODE == KM_FWD_REDUCE || MODE == KM_FWD_STORE) {
-                if (valid) run_tangents(G.ins + G.tan_begin, G.tan_count, C, L.phase_base, n);
-            }
-            for (int o = 0; o < n_out; ++o) {
-                iv F = zero(), Fc = zero();
-                if (valid) {
-                    Fc = C.F.get(L.fc_base + 2 * o);
-                    iv nie;
-                    int gunit, gstride;  // gradient of this output: unit of G_0 and stride (0: constant/variable)
-                    if (MODE == KM_FWD_REDUCE || MODE == KM_FWD_STORE) {
-                        const int rec = L.tan_rec;
-                        const uint32_t kind = G.tan_out_kind[o], ref = G.tan_out_ref[o];
-                        nie = load_val(C, kind, ref, L.phase_base, rec);
-                        if (kind == K_SLOT) { gunit = L.phase_base + (int)ref * rec + 2; gstride = 2; }
-                        else { gunit = (kind == K_VAR) ? (int)ref : -1; gstride = 0; }
-                    } else {
-                        const AdjProgram& A = G.adj[o];
-                        const int gb = L.phase_base, ab = gb + 2 * n, tb = ab + 2 * A.adj_slots;
-                        run_values(G.ins + A.fw_begin, A.fw_count, C, tb);
-                        for (int i = 0; i < n; ++i) C.F.put(gb + 2 * i, zero());
-                        if (A.out_wslot >= 0) C.F.put(ab + 2 * A.out_wslot, one());
-                        run_reverse(G.rins + A.rv_begin, A.rv_count, C, ab, tb, gb);
-                        nie = load_val(C, A.out_kind_ref, A.out_ref, tb, 2);
-                        gunit = gb;
-                        gstride = 2;
-                    }
-                    // Mean Value Form (Definition 5): f(c) + sum_i G_i (X_i - c_i), left to right
-                    iv mvf = Fc;
-                    for (int i = 0; i < n; ++i) {
-                        const iv Gi = gstride ? C.F.get(gunit + 2 * i) : ((gunit == i) ? one() : zero());
-                        const iv Xi = C.F.get(L.x_base + 2 * i);
-                        const double ci = C.F.ld(L.c_base + i);
-                        const iv dx = mk(sub_dn(Xi.lo, ci), sub_up(Xi.hi, ci));
-                        mvf = iv_add(mvf, iv_mul(Gi, dx));
-                        if ((MODE == KM_FWD_STORE || MODE == KM_ADJ_STORE) && P.outG) {
-                            const long long s = g - P.store_first_g;
-                            double* q = P.outG + ((size_t)s * n_out + o) * n * 2 + 2 * i;
-                            q[0] = Gi.lo;
-                            q[1] = Gi.hi;
-                        }
-                    }
-                    F = mvf;
-                    if (P.form == 1) F = nie;
-                    else if (P.form == 2) F = iv_meet(mvf, nie);
-                    if (isnan_(F.lo) || isnan_(F.hi)) F = entire();
-                    const uint8_t kind = G.out_kind[o];
-                    if (kind == OUT_INEQ && gt0(F.lo)) cert_infeasible = true;
-                    if (kind == OUT_EQ && (gt0(F.lo) || lt0(F.hi))) cert_infeasible = true;
-                    if (o == G.obj) obj_lo = F.lo;
-                }
-                if (MODE == KM_FWD_STORE || MODE == KM_ADJ_STORE) {
-                    if (valid) {
-                        const long long s = g - P.store_first_g;
-                        P.outF[((size_t)s * n_out + o) * 2] = F.lo;
-                        P.outF[((size_t)s * n_out + o) * 2 + 1] = F.hi;
-                        if (P.outFc) {
-                            P.outFc[((size_t)s * n_out + o) * 2] = Fc.lo;
-                            P.outFc[((size_t)s * n_out + o) * 2 + 1] = Fc.hi;
-                        }
-                    }
+                Fc = C.F.get(L.fc_base + 2 * o);
+                iv nie;
+                int gunit, gstride;  // gradient of this output: unit of G_0 and stride (0: constant/variable)
+                if (MODE == KM_FWD_REDUCE || MODE == KM_FWD_STORE) {
+                    const int rec = L.tan_rec;
+                    const uint32_t kind = G.tan_out_kind[o], ref = G.tan_out_ref[o];
+                    nie = load_val(C, kind, ref, L.phase_base, rec);
+                    if (kind == K_SLOT) { gunit = L.phase_base + (int)ref * rec + 2; gstride = 2; }
+                    else { gunit = (kind == K_VAR) ? (int)ref : -1; gstride = 0; }
                 } else {
-                    // ---- Step 3: refinement hull per node and output
-                    reduce_key(P.keys, node, o, K, ukey_lo(F.lo), valid, uniform, true);
-                    reduce_key(P.keys, node, n_out + o, K, ukey_hi(F.hi), valid, uniform, false);
+                    const AdjProgram& A = G.adj[o];
+                    const int gb = L.phase_base, ab = gb + 2 * n, tb = ab + 2 * A.adj_slots;
+                    run_values(G.ins + A.fw_begin, A.fw_count, C, tb);
+                    for (int i = 0; i < n; ++i) C.F.put(gb + 2 * i, zero());
+                    if (A.out_wslot >= 0) C.F.put(ab + 2 * A.out_wslot, one());
+                    run_reverse(G.rins + A.rv_begin, A.rv_count, C, ab, tb, gb);
+                    nie = load_val(C, A.out_kind_ref, A.out_ref, tb, 2);
+                    gunit = gb;
+                    gstride = 2;
                 }
+                // Mean Value Form (Definition 5): f(c) + sum_i G_i (X_i - c_i), left to right
+                iv mvf = Fc;
+                for (int i = 0; i < n; ++i) {
+                    const iv Gi = gstride ? C.F.get(gunit + 2 * i) : ((gunit == i) ? one() : zero());
+                    mvf = mvf_term(mvf, Gi, C.F.get(L.x_base + 2 * i), C.F.ld(L.c_base + i));
+                    if ((MODE == KM_FWD_STORE || MODE == KM_ADJ_STORE) && P.outG) {
+                        const long long q0 = g - P.store_first_g;
+                        double* q = P.outG + ((size_t)q0 * n_out + o) * n * 2 + 2 * i;
+                        q[0] = Gi.lo;
+                        q[1] = Gi.hi;
+                    }
+                }
+                F = final_form(P.form, mvf, nie);
+                if (excludes_feasible(G.out_kind[o], F)) cert_infeasible = true;
+                if (o == G.obj) obj_lo = F.lo;
             }
-            if (MODE == KM_FWD_REDUCE || MODE == KM_ADJ_REDUCE) {
-                // certified-feasible centre upper bound and filtered objective minimum
-                double ub = from_bits(0x7FF0000000000000LL);
+            if (MODE == KM_FWD_STORE || MODE == KM_ADJ_STORE) {
                 if (valid) {
-                    bool feas = !G.has_eq;
-                    for (int o = 0; o < n_out; ++o)
-                        if (G.out_kind[o] == OUT_INEQ && !le0(C.F.ld(L.fc_base + 2 * o + 1))) feas = false;
-                    if (feas) ub = C.F.ld(L.fc_base + 2 * G.obj + 1);
-                    if (cert_infeasible) obj_lo = from_bits(0x7FF0000000000000LL);
+                    const long long q0 = g - P.store_first_g;
+                    P.outF[((size_t)q0 * n_out + o) * 2] = F.lo;
+                    P.outF[((size_t)q0 * n_out + o) * 2 + 1] = F.hi;
+                    if (P.outFc) {
+                        P.outFc[((size_t)q0 * n_out + o) * 2] = Fc.lo;
+                        P.outFc[((size_t)q0 * n_out + o) * 2 + 1] = Fc.hi;
+                    }
                 }
-                reduce_key(P.keys, node, 2 * n_out, K, ukey_hi(ub), valid, uniform, true);
-                reduce_key(P.keys, node, 2 * n_out + 1, K, ukey_lo(obj_lo), valid, uniform, true);
+            } else {
+                // ---- Step 3: refinement hull per node and output
+                reduce_output(P, s, n_out, o, F);
             }
         }
-    }
+        if (MODE == KM_FWD_REDUCE || MODE == KM_ADJ_REDUCE) {
+            double ub = from_bits(0x7FF0000000000000LL);
+            if (valid) {
+                bool feas = !G.has_eq;
+                for (int o = 0; o < n_out; ++o)
+                    if (G.out_kind[o] == OUT_INEQ && !le0(C.F.ld(L.fc_base + 2 * o + 1))) feas = false;
+                if (feas) ub = C.F.ld(L.fc_base + 2 * G.obj + 1);
+                if (cert_infeasible) obj_lo = from_bits(0x7FF0000000000000LL);
+            }
+            reduce_extras(P, s, n_out, ub, obj_lo);
+        }
+    });
 }
 
 }  // namespace ivb
@@ -641,6 +547,11 @@ cudaError_t run_own_probe(int which, double* out, int grid, int block, int iters
 
 // exp/log tables in extended precision on the host (long double: 64-bit
 // significand on x86-64, binary128 on AArch64), split into double hi + lo
+cudaError_t math_tables_address(void** ptr, size_t* bytes) {
+    *bytes = sizeof(MathTables);
+    return cudaGetSymbolAddress(ptr, g_math);
+}
+
 cudaError_t init_math_tables() {
     static bool done[256] = {false};
     int dev = 0;

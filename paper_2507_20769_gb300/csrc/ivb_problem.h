@@ -7,6 +7,7 @@
 
 #include "../../include/ivb.h"
 #include "ivb_internal.h"
+#include "ivb_jit.h"
 #include "ivb_kernels.h"
 
 struct ivb_problem {
@@ -45,5 +46,7 @@ struct ivb_problem {
     double* d_pframe = nullptr;
     size_t pframe_bytes = 0;
     long long launches = 0;
+    // tape-specialised reduce kernel (option specialize), unloaded by ivb_destroy
+    ivb::JitKernel jit;
     std::string err;
 };

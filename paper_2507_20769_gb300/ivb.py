@@ -35,7 +35,7 @@ class ivb_options(ctypes.Structure):
     _fields_ = [("grad_mode", ctypes.c_int32), ("form", ctypes.c_int32), ("filter", ctypes.c_int32),
                 ("batched", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("max_nodes", ctypes.c_int32), ("frame_in_shared", ctypes.c_int32)]
+                ("max_nodes", ctypes.c_int32), ("frame_in_shared", ctypes.c_int32), ("specialize", ctypes.c_int32)]
 
 
 class ivb_tape(ctypes.Structure):
@@ -91,9 +91,11 @@ def lib() -> ctypes.CDLL:
         L.ivb_fp64_probe.argtypes = [I32, I32, P]
         L.ivb_bnb_options_default.argtypes = [P]
         L.ivb_bnb_solve.argtypes = [P, I32, P, P, P, P]
+        L.ivb_get_specialization.argtypes = [P, P, P, P, P]
+        L.ivb_specialize_compile.argtypes = [P, I32, P, P, P]
         for f in ("ivb_create_problem", "ivb_bound_nodes", "ivb_bound_nodes_ex", "ivb_enclose", "ivb_point_grad",
                   "ivb_pick_splits", "ivb_get_tuning", "ivb_bnb_solve", "ivb_op_counts", "ivb_fp64_probe",
-                  "ivb_bound_nodes_noalloc", "ivb_eval_op"):
+                  "ivb_bound_nodes_noalloc", "ivb_eval_op", "ivb_get_specialization", "ivb_specialize_compile"):
             getattr(L, f).restype = I32
         _lib = L
     return _lib
@@ -204,6 +206,21 @@ def ivb_eval_op(opcode: int, x, y=None):
     r = torch.empty_like(x)
     _check(lib().ivb_eval_op(int(opcode), int(x.shape[0]), _ptr(x), _ptr(y), _ptr(r), _stream_for(x)))
     return r
+
+
+def ivb_specialize_compile(tape, grad_mode="adjoint") -> dict:
+    """generate and compile (NVRTC, no GPU needed) the tape-specialised
+    kernel of a tape: ptxas registers, spill-store bytes, compile seconds"""
+    recs = tape.records()
+    oi = np.ascontiguousarray(tape.out_idx, dtype=np.int32)
+    ok = np.ascontiguousarray(tape.out_kind, dtype=np.uint8)
+    t = ivb_tape(int(tape.n_vars), int(recs.shape[0]), int(oi.shape[0]), recs.ctypes.data, oi.ctypes.data,
+                 ok.ctypes.data)
+    regs, spill, secs = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    g = GRAD[grad_mode] if isinstance(grad_mode, str) else int(grad_mode)
+    _check(lib().ivb_specialize_compile(ctypes.byref(t), g, ctypes.byref(regs), ctypes.byref(spill),
+                                        ctypes.byref(secs)))
+    return {"registers": regs.value, "spill_bytes": spill.value, "seconds": secs.value}
 
 
 def ivb_last_error(problem=None) -> str:
@@ -340,6 +357,12 @@ class Problem:
         return {"block_threads": v[0].value, "blocks_per_sm": v[1].value, "tile": v[2].value,
                 "frame_in_shared": v[3].value}
 
+    def ivb_get_specialization(self) -> dict:
+        a, r, lb, sec = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        _check(lib().ivb_get_specialization(self._h, ctypes.byref(a), ctypes.byref(r), ctypes.byref(lb),
+                                            ctypes.byref(sec)), self._h)
+        return {"active": bool(a.value), "registers": r.value, "local_bytes": lb.value, "compile_seconds": sec.value}
+
     def ivb_op_counts(self) -> dict:
         c = (ctypes.c_int64 * 8)()
         _check(lib().ivb_op_counts(self._h, c), self._h)
@@ -358,6 +381,7 @@ class Problem:
     point_grad = ivb_point_grad
     bnb_solve = ivb_bnb_solve
     get_tuning = ivb_get_tuning
+    get_specialization = ivb_get_specialization
     launch_count = ivb_launch_count
     op_counts = ivb_op_counts
     bound_nodes_noalloc = ivb_bound_nodes_noalloc

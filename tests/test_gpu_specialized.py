@@ -1,0 +1,153 @@
+"""GPU parity of the tape-specialised bounding kernel (option specialize=1:
+the tape's programs written out as straight-line CUDA and compiled with NVRTC
+at problem creation).
+
+It evaluates the same interval primitives on the same operands in the same
+accumulation order as the tape interpreter, so every result must equal the
+interpreter's bit for bit, and on rational tapes the oracle's bit for bit."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import problems as P
+from paper_2507_20769_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2507_20769_gb300 import build as B  # noqa: E402
+
+B.build()
+from paper_2507_20769_gb300 import ivb  # noqa: E402
+
+KEYS = ("lb", "ub", "minlo", "maxhi", "infeasible")
+
+
+def rational_problem(n=3, K=60, n_ineq=2, seed=777):
+    return W.random_problem(n, K, n_ineq, W.OPS_RATIONAL, [[-3, 2]] * n, seed, "rational")
+
+
+def ragged_batch(t, n_nodes, seed, max_split=6):
+    rng = np.random.default_rng(seed)
+    boxes = W.bisection_frontier(t.root_box, n_nodes, seed=seed)
+    splits = rng.integers(1, max_split + 1, (n_nodes, t.n_vars)).astype(np.int32)
+    splits[0] = 1                          # S = 1
+    boxes[1, 0, 1] = boxes[1, 0, 0]        # degenerate dimension
+    return boxes, splits
+
+
+def same_bits(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return a.shape == b.shape and np.array_equal(a.view(np.uint8), b.view(np.uint8))
+
+
+def bound_both(t, boxes, splits, **opts):
+    """results of the interpreter and of the specialised kernel, same options"""
+    out = []
+    for spec in (0, 1):
+        with ivb.Problem(t, specialize=spec, **opts) as p:
+            if spec:
+                assert p.get_specialization()["active"]
+            out.append(p.bound_nodes_ex(boxes, splits, want_hull=True))
+    return out
+
+
+@pytest.mark.parametrize("grad_mode", ["forward", "adjoint"])
+@pytest.mark.parametrize("path", ["graph", "nograph", "plain"])
+def test_specialized_bit_exact_rational_vs_oracle(grad_mode, path):
+    """ragged batch (S from 1 to 216 per node, tiles crossing nodes), every
+    launch path: lb, infeasibility, centre upper bound and each output's hull
+    equal the oracle's bit for bit"""
+    t = rational_problem()
+    boxes, splits = ragged_batch(t, 37, seed=11)
+    opts = dict(grad_mode=grad_mode, use_graph=int(path == "graph"), batched=int(path != "plain"), specialize=1)
+    with ivb.Problem(t, **opts) as p:
+        assert p.get_specialization()["active"]
+        r = p.bound_nodes_ex(boxes, splits, want_hull=True)
+        r2 = p.bound_nodes_ex(boxes, splits, want_hull=True)
+    ref = oracle.bound_nodes(t, boxes, splits, grad_mode=grad_mode, tight=True)
+    for rr in (r, r2):
+        for k in ("lb", "ub", "minlo", "maxhi"):
+            assert np.array_equal(rr[k], ref[k]), k
+        assert np.array_equal(rr["infeasible"].astype(bool), ref["infeasible"])
+
+
+@pytest.mark.parametrize("grad_mode", ["forward", "adjoint"])
+@pytest.mark.parametrize("form", ["mvf", "nie", "mvf_nie"])
+def test_specialized_identical_to_interpreter_exp_log(grad_mode, form):
+    """configuration 1 (exp/log tape): all results bit-identical to the interpreter"""
+    t = W.config_tape(1)
+    boxes, splits = ragged_batch(t, 23, seed=5, max_split=40)
+    a, b = bound_both(t, boxes, splits, grad_mode=grad_mode, form=form)
+    for k in KEYS:
+        assert same_bits(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("kind", ["feasible", "infeasible", "eq_out", "eq_in"])
+@pytest.mark.parametrize("filt", [0, 1])
+def test_specialized_feasibility_filter_and_ub_match_oracle(kind, filt):
+    t = P.constrained_toy(kind)
+    boxes = W.bisection_frontier(t.root_box, 9, seed=2)
+    splits = np.array([[6, 5]] * 9, np.int32)
+    with ivb.Problem(t, filter=filt, specialize=1) as p:
+        r = p.bound_nodes_ex(boxes, splits, want_hull=True)
+    ref = oracle.bound_nodes(t, boxes, splits, filter=bool(filt))
+    assert np.array_equal(r["lb"], ref["lb"])
+    assert np.array_equal(r["infeasible"].astype(bool), ref["infeasible"])
+    assert np.array_equal(r["ub"], ref["ub"])
+
+
+def variable_and_constant_outputs():
+    """objective that is a variable entry itself, an inequality that is a
+    constant entry, and an equality sharing the objective's variable: the
+    generator's special cases (gradient e_i, no adjoint slot, a product of an
+    entry with itself, a negation)"""
+    Bd = P.Builder(2)
+    x0, x1 = Bd.x(0), Bd.x(1)
+    Bd.output(x0, P.KIND_OBJ)
+    Bd.output(Bd.const(-0.5), P.KIND_INEQ)
+    Bd.output(Bd.sub(Bd.mul(x0, x0), Bd.neg(x1)), P.KIND_EQ)
+    return Bd.tape([[-1.0, 2.0], [-1.5, 1.0]], "variable and constant outputs")
+
+
+@pytest.mark.parametrize("grad_mode", ["forward", "adjoint"])
+def test_specialized_variable_and_constant_outputs(grad_mode):
+    t = variable_and_constant_outputs()
+    boxes, splits = ragged_batch(t, 11, seed=4)
+    a, b = bound_both(t, boxes, splits, grad_mode=grad_mode)
+    for k in KEYS:
+        assert same_bits(a[k], b[k]), k
+    ref = oracle.bound_nodes(t, boxes, splits, grad_mode=grad_mode, tight=True)
+    for k in ("lb", "ub", "minlo", "maxhi"):
+        assert np.array_equal(b[k], ref[k]), k
+
+
+def test_specialized_full_size_config2_identical_to_interpreter():
+    """configuration 2 at full size (16 nodes x 16^4 subdomains, autotuned,
+    CUDA graph): bit-identical to the interpreter"""
+    wl = W.config_workload(2)
+    t = wl.tape
+    boxes = W.bisection_frontier(t.root_box, 16, seed=20)
+    splits = np.tile(wl.splits, (16, 1)).astype(np.int32)
+    a, b = bound_both(t, boxes, splits)
+    for k in KEYS:
+        assert same_bits(a[k], b[k]), k
+
+
+def test_specialize_auto_info_and_empty_batch():
+    """specialize=-1 compiles a small tape and leaves a large one (configuration
+    5, above the size limit) to the interpreter; an empty batch is a no-op"""
+    with ivb.Problem(W.config_tape(1), specialize=-1) as p:
+        info = p.get_specialization()
+        assert info["active"] and 0 < info["registers"] <= 128 and info["compile_seconds"] > 0
+        r = p.bound_nodes_ex(np.zeros((0, 2, 2)), np.zeros((0, 2), np.int32))
+        assert r["lb"].shape == (0,)
+    with ivb.Problem(W.config_tape(5), specialize=-1) as p:
+        assert not p.get_specialization()["active"]
+    with ivb.Problem(W.config_tape(1)) as p:
+        assert not p.get_specialization()["active"]
