@@ -114,6 +114,14 @@ typedef struct {
                                   -1: specialise when the tape is small enough
                                   for a short compile (at most 4096 interval
                                   operations per subdomain), else interpret  */
+    int32_t emulate;           /* tape-specialised kernel only: endpoint
+                                  operations computed by an exact emulation
+                                  on the integer pipes (bit-identical to the
+                                  FP64 instructions), running beside the
+                                  narrow FP64 pipe. Bitmask: 1 upper ends of
+                                  products, 2 lower ends of products, 4 upper
+                                  ends of sums and differences, 8 lower ends;
+                                  -1 (default): the library's choice       */
 } ivb_options;
 
 typedef struct ivb_problem ivb_problem;
@@ -233,6 +241,18 @@ typedef struct {
     int64_t max_nodes;         /* limit on bounded nodes (0 = none)         */
     double time_limit;         /* seconds (0 = none)                        */
     int32_t corner_ub;         /* 1: descent-corner upper bounds (default)  */
+    int32_t propagate;         /* > 0: rounds of constraint propagation
+                                  (forward-backward bound tightening against
+                                  the constraints and f <= UB, on the host)
+                                  applied to every box before it is bounded;
+                                  boxes proven empty are dropped (0 default) */
+    int32_t overlap;           /* 1: keep the GPU busy while the host works:
+                                  the next batch is selected and enqueued
+                                  before the results of the batch in flight
+                                  are absorbed, so branching, propagation and
+                                  upper bounding on the host overlap the
+                                  bounding kernel (best-first order lags one
+                                  batch); 0 (default): one batch at a time  */
 } ivb_bnb_options;
 
 typedef struct {
@@ -246,6 +266,17 @@ typedef struct {
 } ivb_bnb_result;
 
 void ivb_bnb_options_default(ivb_bnb_options* o);
+
+/* Constraint propagation on the host, no GPU needed: forward-backward bound
+ * tightening (HC4-style projections through every operation) of n_boxes
+ * boxes [n_boxes][n_vars][2] against the tape's inequalities (g <= 0),
+ * equalities (h = 0) and f <= ub (ub = +inf: no objective cut), for at most
+ * `passes` rounds (fewer when a round changes nothing). boxes_out receives
+ * the tightened boxes (never wider than the input), infeasible[k] = 1 when
+ * box k provably holds no such point. Outward-rounded on the CPU with the
+ * kernels' interval rules. */
+ivb_status ivb_propagate(const ivb_tape* tape, int32_t n_boxes, const double* boxes, double ub,
+                         int32_t passes, double* boxes_out, uint8_t* infeasible);
 /* root: host array [n][2]; n must equal the problem's n_vars. */
 ivb_status ivb_bnb_solve(ivb_problem* p, int32_t n, const double* root, const ivb_bnb_options* opt,
                          ivb_bnb_result* result, void* cuda_stream);
@@ -255,12 +286,12 @@ ivb_status ivb_bnb_solve(ivb_problem* p, int32_t n, const double* root, const iv
 ivb_status ivb_get_tuning(ivb_problem* p, int32_t* block_threads, int32_t* blocks_per_sm,
                           int32_t* tile, int32_t* frame_in_shared);
 
-/* The tape-specialised kernel of a problem (may be NULL): active (0/1),
+/* The tape-specialised kernel of a problem (each may be NULL): active (0/1),
  * registers per thread, local memory bytes per thread, NVRTC compile time in
- * seconds. Not part of the paper's method: reports how the bounds are
- * computed, not what they are. */
+ * seconds, emulation policy compiled in. Not part of the paper's method:
+ * reports how the bounds are computed, not what they are. */
 ivb_status ivb_get_specialization(ivb_problem* p, int32_t* active, int32_t* registers,
-                                  int32_t* local_bytes, double* compile_seconds);
+                                  int32_t* local_bytes, double* compile_seconds, int32_t* emulate);
 
 /* Generate and compile (NVRTC, sm_103a) the tape-specialised kernel of a
  * tape without loading it -- needs no GPU. Reports ptxas' registers per
@@ -289,21 +320,31 @@ ivb_status ivb_op_counts(const ivb_problem* p, int64_t counts[IVB_CNT_N]);
  * this library's kernels use (one directed end each, outward widening of
  * exp/log included) and give the cost of each category of ivb_op_counts in
  * DFMA issue slots. Both LOG probes include one round-to-nearest add and both
- * SQRT probes one round-to-nearest multiply. */
+ * SQRT probes one round-to-nearest multiply. EMU_MUL / EMU_ADD run the
+ * integer-pipe emulation of the directed multiply / add (option `emulate`);
+ * MIXED_* run half the chains on the FP64 pipe and half emulated, side by
+ * side. */
 enum {
     IVB_PROBE_DADD = 0, IVB_PROBE_DMUL = 1, IVB_PROBE_DFMA = 2, IVB_PROBE_DDIV = 3,
     IVB_PROBE_DRCP = 4, IVB_PROBE_DSQRT = 5, IVB_PROBE_EXP = 6, IVB_PROBE_LOG = 7,
     IVB_PROBE_OWN_RCP = 8, IVB_PROBE_OWN_DIV = 9, IVB_PROBE_OWN_SQRT = 10,
-    IVB_PROBE_OWN_EXP = 11, IVB_PROBE_OWN_LOG = 12
+    IVB_PROBE_OWN_EXP = 11, IVB_PROBE_OWN_LOG = 12, IVB_PROBE_EMU_MUL = 13,
+    IVB_PROBE_MIXED_MUL = 14, IVB_PROBE_EMU_ADD = 15, IVB_PROBE_MIXED_ADD = 16
 };
 ivb_status ivb_fp64_probe(int32_t which, int32_t iters, double* lane_ops_per_s);
 
 /* Test hook: one interval operation of the bounding kernels' own arithmetic
  * (the natural interval extension of an intrinsic, Section 2.2, with this
  * library's outward rounding) on n intervals: x, y, r are DEVICE arrays
- * [n][2]; opcode is a binary or unary tape opcode, or IVB_EVAL_RECIP for the
- * interval reciprocal 1/x. Enqueued on cuda_stream. */
+ * [n][2]; opcode is a binary or unary tape opcode, IVB_EVAL_RECIP for the
+ * interval reciprocal 1/x, or IVB_EVAL_EMU_* for +, -, *, sqr with every
+ * endpoint operation done by the integer-pipe emulation (option `emulate`).
+ * Enqueued on cuda_stream. */
 #define IVB_EVAL_RECIP 100
+#define IVB_EVAL_EMU_ADD 101
+#define IVB_EVAL_EMU_SUB 102
+#define IVB_EVAL_EMU_MUL 103
+#define IVB_EVAL_EMU_SQR 104
 ivb_status ivb_eval_op(int32_t opcode, int64_t n, const double* x, const double* y, double* r,
                        void* cuda_stream);
 

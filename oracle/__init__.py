@@ -72,7 +72,8 @@ def lib() -> ctypes.CDLL:
         L.orc_log_enclose.argtypes = [I64, P, I, P, P]
         L.orc_iv_op.argtypes = [I, I64, P, P, I, P]
         L.orc_pick_splits.argtypes = [I, P, P, I64, I, P]
-        L.orc_bnb.argtypes = [I, I, I, P, P, P, P, P, P, P, P, I64, I, I, I, I, D, D, I64, D, I, P]
+        L.orc_bnb.argtypes = [I, I, I, P, P, P, P, P, P, P, P, I64, I, I, I, I, D, D, I64, D, I, I, P]
+        L.orc_propagate.argtypes = [I, I, I, P, P, P, P, P, P, I64, P, D, I, I, P]
         L.orc_set_threads.argtypes = [I]
         L.orc_max_threads.restype = I
         _lib = L
@@ -230,16 +231,29 @@ def pick_splits(box, target: int, strategy: str = "adaptive", ref=None):
 
 def bnb(t, root=None, splits=None, target: int = 0, strategy: str = "adaptive", grad_mode: str = "adjoint",
         form: str = "mvf", tight: bool = False, eps_abs: float = 0.0, eps_rel: float = 1e-3,
-        max_nodes: int = 0, time_limit: float = 0.0, corner_ub: bool = True):
-    """best-first B&B with the oracle as lower-bounding solver"""
+        max_nodes: int = 0, time_limit: float = 0.0, corner_ub: bool = True, propagate: int = 0):
+    """best-first B&B with the oracle as lower-bounding solver; propagate > 0:
+    tighten every box by that many rounds of constraint propagation first"""
     a, b, c, op, oi, ok = _tape_args(t)
     root = _f64(t.root_box if root is None else root)
     sp = _i32(splits if splits is not None else np.ones(t.n_vars, np.int32))
     stats = np.empty(8)
     rc = lib().orc_bnb(t.n_vars, t.n_ops, t.n_out, _p(op), _p(a), _p(b), _p(c), _p(oi), _p(ok), _p(root), _p(sp),
                        int(target), STRATEGY[strategy], GRAD[grad_mode], FORM[form], int(tight), float(eps_abs),
-                       float(eps_rel), int(max_nodes), float(time_limit), int(corner_ub), _p(stats))
+                       float(eps_rel), int(max_nodes), float(time_limit), int(corner_ub), int(propagate), _p(stats))
     assert rc == 0
     return {"lb": stats[0], "ub": stats[1], "iterations": int(stats[2]), "nodes": int(stats[3]),
             "subdomains": int(stats[4]), "seconds": stats[5], "converged": bool(stats[6]),
             "open": int(stats[7])}
+
+
+def propagate(t, boxes, ub: float = float("inf"), passes: int = 4, tight: bool = True):
+    """forward-backward bound tightening of boxes [..., n, 2] against the
+    tape's constraints and f <= ub: (tightened boxes, infeasible flags)"""
+    a, b, c, op, oi, ok = _tape_args(t)
+    bx = np.array(_f64(boxes).reshape(-1, t.n_vars, 2))
+    inf = np.empty(bx.shape[0], dtype=np.uint8)
+    rc = lib().orc_propagate(t.n_vars, t.n_ops, t.n_out, _p(op), _p(a), _p(b), _p(c), _p(oi), _p(ok),
+                             bx.shape[0], _p(bx), float(ub), int(passes), int(tight), _p(inf))
+    assert rc == 0
+    return bx, inf.astype(bool)

@@ -820,6 +820,122 @@ int orc_pick_splits(int n, const double* box, const double* ref, int64_t target,
     return 0;
 }
 
+/* ------------------------------------------------- constraint propagation
+ * Forward-backward bound tightening of a node box (host side of the B&B,
+ * next to the paper's constraint propagation in its B&B framework): the
+ * natural interval extension gives every entry an interval on the box; the
+ * outputs are intersected with what a solution must satisfy (inequality
+ * g <= 0, equality h = 0, objective f <= ub); then each entry, from the last
+ * to the first, passes its interval back to its operands through the
+ * inverse of its operation (HC4-style projections), each intersected with
+ * what the operand had:
+ *   z = a + b : a in z - b, then b in z - a      z = a - b : a in z + b, then b in a - z
+ *   z = a * b : a in z / b if 0 not in b, then b in z / a if 0 not in a
+ *   z = a / b : a in z * b, then b in a / z if 0 not in z
+ *   z = a^2   : |a| <= sqrt(z.hi), and |a| >= sqrt(z.lo) when a has one sign
+ *   z = sqrt a: a in [z.lo^2, z.hi^2] (lower end -inf unless z.lo > 0)
+ *   z = exp a : a in [log z.lo, log z.hi] (lower end -inf unless z.lo > 0)
+ *   z = log a : a in [exp z.lo, exp z.hi]         z = -a : a in -z
+ *   variable  : the box's dimension is intersected with z
+ *   constant  : z must contain it
+ * NaN endpoints mean no information. A round repeats the forward sweep on the
+ * tightened box; at most `passes` rounds, stopping early when a round leaves
+ * the box bit-for-bit unchanged. Returns 1 when an intersection is empty. */
+static int meet_iv(iv* x, iv y) {
+    if (isnan(y.lo) || isnan(y.hi)) return 1;
+    if (y.lo > x->lo) x->lo = y.lo;
+    if (y.hi < x->hi) x->hi = y.hi;
+    return x->lo <= x->hi;
+}
+static int straddles0(iv x) { return !(x.lo > 0.0 || x.hi < 0.0); }
+
+static int propagate_box(const tape_t* T, double* box, double ub, int passes, int tight, iv* X, iv* V,
+                         double* before) {
+    const int n = T->n_vars;
+    for (int pass = 0; pass < passes; ++pass) {
+        memcpy(before, box, (size_t)2 * n * sizeof(double));
+        for (int i = 0; i < n; ++i) { X[i].lo = box[2 * i]; X[i].hi = box[2 * i + 1]; }
+        value_sweep(T, X, V, tight);
+        for (int t = 0; t < T->n_ops; ++t)
+            if (isnan(V[t].lo) || isnan(V[t].hi)) V[t] = ENTIRE;
+        for (int q = 0; q < T->n_out; ++q) {
+            iv* z = &V[T->out_idx[q]];
+            int ok = 1;
+            if (T->out_kind[q] == KIND_INEQ) { iv g = {-INFINITY, 0.0}; ok = meet_iv(z, g); }
+            else if (T->out_kind[q] == KIND_EQ) ok = meet_iv(z, ZERO);
+            else if (ub < INFINITY) { iv f = {-INFINITY, ub}; ok = meet_iv(z, f); }
+            if (!ok) return 1;
+        }
+        for (int t = T->n_ops - 1; t >= 0; --t) {
+            const int a = T->a[t], b = T->b[t];
+            const iv z = V[t];
+            int ok = 1;
+            switch (T->op[t]) {
+            case OP_VAR: {
+                iv x = {box[2 * a], box[2 * a + 1]};
+                ok = meet_iv(&x, z);
+                box[2 * a] = x.lo;
+                box[2 * a + 1] = x.hi;
+            } break;
+            case OP_CONST: ok = z.lo <= T->c[t] && T->c[t] <= z.hi; break;
+            case OP_ADD: ok = meet_iv(&V[a], iv_sub(z, V[b])) && meet_iv(&V[b], iv_sub(z, V[a])); break;
+            case OP_SUB: ok = meet_iv(&V[a], iv_add(z, V[b])) && meet_iv(&V[b], iv_sub(V[a], z)); break;
+            case OP_NEG: ok = meet_iv(&V[a], iv_neg(z)); break;
+            case OP_MUL:
+                if (!straddles0(V[b])) ok = meet_iv(&V[a], iv_div(z, V[b]));
+                if (ok && !straddles0(V[a])) ok = meet_iv(&V[b], iv_div(z, V[a]));
+                break;
+            case OP_DIV:
+                ok = meet_iv(&V[a], iv_mul(z, V[b]));
+                if (ok && !straddles0(z)) ok = meet_iv(&V[b], iv_div(V[a], z));
+                break;
+            case OP_SQR: {
+                if (z.hi < 0.0) { ok = 0; break; }
+                const double r_hi = sqrt_up(z.hi);
+                const double r_lo = z.lo > 0.0 ? sqrt_dn(z.lo) : 0.0;
+                iv r;
+                if (V[a].lo >= 0.0) { r.lo = r_lo; r.hi = r_hi; }
+                else if (V[a].hi <= 0.0) { r.lo = -r_hi; r.hi = -r_lo; }
+                else { r.lo = -r_hi; r.hi = r_hi; }
+                ok = meet_iv(&V[a], r);
+            } break;
+            case OP_SQRT: {
+                if (z.hi < 0.0) { ok = 0; break; }
+                iv r = {z.lo > 0.0 ? prod_dn(z.lo, z.lo) : -INFINITY, prod_up(z.hi, z.hi)};
+                ok = meet_iv(&V[a], r);
+            } break;
+            case OP_EXP: {
+                if (!(z.hi > 0.0)) { ok = 0; break; }
+                iv r = {z.lo > 0.0 ? log_dn(z.lo, tight) : -INFINITY, log_up(z.hi, tight)};
+                ok = meet_iv(&V[a], r);
+            } break;
+            case OP_LOG: {
+                iv r = {exp_dn(z.lo, tight), exp_up(z.hi, tight)};
+                ok = meet_iv(&V[a], r);
+            } break;
+            }
+            if (!ok) return 1;
+        }
+        if (memcmp(before, box, (size_t)2 * n * sizeof(double)) == 0) break;
+    }
+    return 0;
+}
+
+/* boxes [count][n][2] tightened in place; infeasible[count] */
+int orc_propagate(int n_vars, int n_ops, int n_out, const uint8_t* op, const int32_t* a, const int32_t* b,
+                  const double* c, const int32_t* out_idx, const uint8_t* out_kind, int64_t count, double* boxes,
+                  double ub, int passes, int tight, uint8_t* infeasible) {
+    tape_t T = make_tape(n_vars, n_ops, n_out, op, a, b, c, out_idx, out_kind);
+    iv* X = malloc((size_t)n_vars * sizeof(iv));
+    iv* V = malloc((size_t)n_ops * sizeof(iv));
+    double* before = malloc((size_t)2 * n_vars * sizeof(double));
+    if (!X || !V || !before) { free(X); free(V); free(before); return 2; }
+    for (int64_t k = 0; k < count; ++k)
+        infeasible[k] = (uint8_t)propagate_box(&T, boxes + (size_t)k * 2 * n_vars, ub, passes, tight, X, V, before);
+    free(X); free(V); free(before);
+    return 0;
+}
+
 /* ---------------------------------------------------------- branch & bound
  * Best-first spatial B&B (Section 3, Fig. 3) with the oracle's bounding as
  * lower-bounding solver. Each iteration pops the open node of lowest lower
@@ -835,7 +951,11 @@ int orc_pick_splits(int n, const double* box, const double* ref, int64_t target,
  * UB - min(open lb) <= that tolerance, the heap is empty, or a node / time
  * limit is reached; the final lower bound is min(open lb, lb of nodes
  * dropped by the bound test). Splits per node: the fixed vector `splits` if
- * target <= 0, else orc_pick_splits(target, strategy). */
+ * target <= 0, else orc_pick_splits(target, strategy). With propagate > 0
+ * each box (root and children) is first tightened by that many rounds of
+ * constraint propagation against the constraints and f <= UB (the UB before
+ * the batch); a box proven empty is dropped unbounded and takes no part in
+ * the incumbent update. */
 typedef struct { double lb; double* box; } bb_node;
 
 static void heap_push(bb_node* h, int64_t* n, bb_node x) {
@@ -924,14 +1044,21 @@ static double bb_corner_value(const tape_t* T, const double* box, int grad_mode,
 int orc_bnb(int n_vars, int n_ops, int n_out, const uint8_t* op, const int32_t* a, const int32_t* b,
             const double* c, const int32_t* out_idx, const uint8_t* out_kind, const double* root,
             const int32_t* splits, int64_t target, int strategy, int grad_mode, int form, int tight,
-            double eps_abs, double eps_rel, int64_t max_nodes, double time_limit, int corner_ub, double* stats) {
+            double eps_abs, double eps_rel, int64_t max_nodes, double time_limit, int corner_ub, int propagate,
+            double* stats) {
     const int n = n_vars;
     tape_t T = make_tape(n_vars, n_ops, n_out, op, a, b, c, out_idx, out_kind);
     int64_t cap = 1024, n_open = 0;
     bb_node* heap = malloc((size_t)cap * sizeof(bb_node));
     double* ref = malloc((size_t)n * sizeof(double));
     int32_t* sp = malloc((size_t)n * sizeof(int32_t));
-    if (!heap || !ref || !sp) { free(heap); free(ref); free(sp); return 2; }
+    iv* pX = malloc((size_t)n * sizeof(iv));
+    iv* pV = malloc((size_t)n_ops * sizeof(iv));
+    double* pB = malloc((size_t)2 * n * sizeof(double));
+    if (!heap || !ref || !sp || !pX || !pV || !pB) {
+        free(heap); free(ref); free(sp); free(pX); free(pV); free(pB);
+        return 2;
+    }
     for (int i = 0; i < n; ++i) ref[i] = root[2 * i + 1] - root[2 * i];
     double UB = INFINITY, t0 = now_s();
     int64_t iters = 0, bounded = 0, subs = 0;
@@ -939,22 +1066,30 @@ int orc_bnb(int n_vars, int n_ops, int n_out, const uint8_t* op, const int32_t* 
     double lb_global = -INFINITY, lb_pruned = INFINITY;
     double* kbox[2];
     double klb[2], kub[2];
-    uint8_t kinf[2];
+    uint8_t kinf[2], kdrop[2];
 
-    /* bound one box: lb, infeasible flag, centre ub */
-    #define BOUND(BOX, LB, INF, UBV)                                                               \
+    /* bound one box: lb, infeasible flag, centre ub; with propagation the box
+     * is first tightened against the constraints and f <= UB, and a box
+     * proven empty is marked infeasible without being bounded */
+    #define BOUND(BOX, LB, INF, UBV, DROP)                                                         \
         do {                                                                                       \
+            (DROP) = 0;                                                                            \
+            if (propagate > 0 && propagate_box(&T, (BOX), UB, propagate, tight, pX, pV, pB)) {    \
+                (LB) = INFINITY; (INF) = 1; (UBV) = INFINITY; (DROP) = 1; break;                  \
+            }                                                                                      \
             if (target > 0) orc_pick_splits(n, (BOX), ref, target, strategy, sp);                 \
             else memcpy(sp, splits, (size_t)n * sizeof(int32_t));                                 \
             err |= orc_bound_nodes(n, n_ops, n_out, op, a, b, c, out_idx, out_kind, 1, (BOX), sp, \
                                    grad_mode, form, tight, 0, &(LB), &(INF), &(UBV), NULL, NULL);  \
             bounded++; subs += n_subdomains(n, sp);                                               \
         } while (0)
-    /* incumbent update from a batch of bounded boxes, then push or drop each */
+    /* incumbent update from a batch of bounded boxes, then push or drop each;
+     * boxes emptied by propagation take no part */
     #define ABSORB(CNT)                                                                            \
         do {                                                                                       \
             int best_ = -1;                                                                        \
             for (int k_ = 0; k_ < (CNT); ++k_) {                                                   \
+                if (kdrop[k_]) continue;                                                           \
                 if (kub[k_] < UB) UB = kub[k_];                                                    \
                 if (best_ < 0 || kub[k_] < kub[best_]) best_ = k_;                                 \
             }                                                                                      \
@@ -976,7 +1111,7 @@ int orc_bnb(int n_vars, int n_ops, int n_out, const uint8_t* op, const int32_t* 
 
     kbox[0] = malloc((size_t)n * 2 * sizeof(double));
     memcpy(kbox[0], root, (size_t)n * 2 * sizeof(double));
-    BOUND(kbox[0], klb[0], kinf[0], kub[0]);
+    BOUND(kbox[0], klb[0], kinf[0], kub[0], kdrop[0]);
     ABSORB(1);
     while (n_open > 0) {
         const double tol = fmax(eps_abs, eps_rel * fabs(UB));
@@ -999,8 +1134,8 @@ int orc_bnb(int n_vars, int n_ops, int n_out, const uint8_t* op, const int32_t* 
         memcpy(kbox[0], nd.box, (size_t)n * 2 * sizeof(double));
         kbox[0][2 * bi + 1] = mid;
         kbox[1][2 * bi] = mid;
-        BOUND(kbox[0], klb[0], kinf[0], kub[0]);
-        BOUND(kbox[1], klb[1], kinf[1], kub[1]);
+        BOUND(kbox[0], klb[0], kinf[0], kub[0], kdrop[0]);
+        BOUND(kbox[1], klb[1], kinf[1], kub[1], kdrop[1]);
         ABSORB(2);
     }
     #undef BOUND
@@ -1011,6 +1146,6 @@ int orc_bnb(int n_vars, int n_ops, int n_out, const uint8_t* op, const int32_t* 
     stats[0] = lb_global; stats[1] = UB; stats[2] = (double)iters; stats[3] = (double)bounded;
     stats[4] = (double)subs; stats[5] = now_s() - t0; stats[6] = converged; stats[7] = (double)n_open;
     for (int64_t i = 0; i < n_open; ++i) free(heap[i].box);
-    free(heap); free(ref); free(sp);
+    free(heap); free(ref); free(sp); free(pX); free(pV); free(pB);
     return err;
 }

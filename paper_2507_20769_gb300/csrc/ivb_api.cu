@@ -323,7 +323,8 @@ ivb_status deliver(ivb_problem* p, int n_nodes, double* out_lb, uint8_t* out_inf
 // generate, compile and load the tape-specialised reduce kernel
 cudaError_t specialize(ivb_problem* p, const std::vector<Ins>& ins, const std::vector<RIns>& rins,
                        const std::vector<double>& consts, int mode, std::string* msg) {
-    const std::string src = jit_source(p->P, ins, rins, consts, mode, kJitBlockMax, kJitMinBlocks);
+    const int emu = p->opt.emulate >= 0 ? p->opt.emulate : kJitDefaultEmulate;
+    const std::string src = jit_source(p->P, ins, rins, consts, mode, kJitBlockMax, kJitMinBlocks, emu);
     std::vector<char> cubin;
     std::string tables;
     double secs = 0.0;
@@ -332,6 +333,7 @@ cudaError_t specialize(ivb_problem* p, const std::vector<Ins>& ins, const std::v
     const cudaError_t ce = jit_load(cubin, tables, p->jit);
     if (ce != cudaSuccess) return ce;
     p->jit.mode = mode;
+    p->jit.emulate = emu;
     p->jit.block_max = kJitBlockMax;
     p->jit.compile_seconds = secs;
     return cudaSuccess;
@@ -351,6 +353,7 @@ extern "C" void ivb_options_default(ivb_options* o) {
     o->max_nodes = 4096;
     o->frame_in_shared = -1;
     o->specialize = 0;
+    o->emulate = -1;
 }
 
 extern "C" ivb_status ivb_create_problem(const ivb_tape* tape, const ivb_options* opt, ivb_problem** out) {
@@ -368,6 +371,7 @@ extern "C" ivb_status ivb_create_problem(const ivb_tape* tape, const ivb_options
     if (o.block_threads < 0 || o.block_threads > 512 || (o.block_threads % 32))
         return fail(nullptr, IVB_EINVAL, "block_threads must be a multiple of 32 up to 512 (0 = auto)");
     if (o.specialize < -1 || o.specialize > 1) return fail(nullptr, IVB_EINVAL, "specialize must be -1, 0 or 1");
+    if (o.emulate < -1 || o.emulate > 15) return fail(nullptr, IVB_EINVAL, "emulate must be -1 or a bitmask in [0, 15]");
     if (o.specialize && o.block_threads > kJitBlockMax)
         return fail(nullptr, IVB_EINVAL, "block_threads above 256 with a tape-specialised kernel");
     ivb_problem* p = new ivb_problem();
@@ -383,6 +387,7 @@ extern "C" ivb_status ivb_create_problem(const ivb_tape* tape, const ivb_options
     for (int i = 0; i < p->n_out; ++i) p->out_kind[i] = tape->out_kind[i];
     p->max_nodes = o.max_nodes;
     p->rec_bytes = queue_rec_bytes(p->n);
+    host_tape(tape, p->host);
 
     auto bail = [&](cudaError_t ce, const char* where) {
         std::string m = std::string(where) + ": " + cudaGetErrorString(ce);
@@ -473,16 +478,35 @@ extern "C" ivb_status ivb_create_problem(const ivb_tape* tape, const ivb_options
     return IVB_OK;
 }
 
+namespace {
+ivb_status bound_nodes_impl(ivb_problem* p, int32_t n_nodes, const double* boxes, const int32_t* splits_per_dim,
+                            double* out_lb, uint8_t* out_infeasible, double* out_ub, double* out_minlo,
+                            double* out_maxhi, cudaStream_t s, bool wait_host);
+}  // namespace
+
 extern "C" ivb_status ivb_bound_nodes_ex(ivb_problem* p, int32_t n_nodes, const double* boxes,
                                          const int32_t* splits_per_dim, double* out_lb, uint8_t* out_infeasible,
                                          double* out_ub, double* out_minlo, double* out_maxhi, void* cuda_stream) {
+    return bound_nodes_impl(p, n_nodes, boxes, splits_per_dim, out_lb, out_infeasible, out_ub, out_minlo, out_maxhi,
+                            (cudaStream_t)cuda_stream, true);
+}
+
+ivb_status bound_nodes_enqueue(ivb_problem* p, int32_t n_nodes, const double* boxes, const int32_t* splits,
+                               double* out_lb, uint8_t* out_inf, double* out_ub, double* out_minlo,
+                               double* out_maxhi, cudaStream_t s) {
+    return bound_nodes_impl(p, n_nodes, boxes, splits, out_lb, out_inf, out_ub, out_minlo, out_maxhi, s, false);
+}
+
+namespace {
+ivb_status bound_nodes_impl(ivb_problem* p, int32_t n_nodes, const double* boxes, const int32_t* splits_per_dim,
+                            double* out_lb, uint8_t* out_infeasible, double* out_ub, double* out_minlo,
+                            double* out_maxhi, cudaStream_t s, bool wait_host) {
     if (!p) return fail(nullptr, IVB_EINVAL, "problem handle is NULL");
     p->err.clear();
     if (n_nodes == 0) return IVB_OK;   // empty batch: nothing to bound
     if (n_nodes < 0 || n_nodes > p->max_nodes)
         return fail(p, IVB_EINVAL, "n_nodes must be in [0, max_nodes]");
     if (!boxes || !splits_per_dim) return fail(p, IVB_EINVAL, "boxes and splits_per_dim must not be NULL");
-    cudaStream_t s = (cudaStream_t)cuda_stream;
     size_t qbytes = 0;
     long long total = 0;
     ivb_status st = stage_queue(p, n_nodes, boxes, splits_per_dim, 0, 0, false, &qbytes, &total, s);
@@ -564,9 +588,10 @@ extern "C" ivb_status ivb_bound_nodes_ex(ivb_problem* p, int32_t n_nodes, const 
     }
     st = deliver(p, n_nodes, out_lb, out_infeasible, out_ub, out_minlo, out_maxhi, s, &host_out);
     if (st) return st;
-    if (host_out) CK(cudaStreamSynchronize(s));
+    if (host_out && wait_host) CK(cudaStreamSynchronize(s));
     return IVB_OK;
 }
+}  // namespace
 
 extern "C" ivb_status ivb_bound_nodes(ivb_problem* p, int32_t n_nodes, const double* boxes,
                                       const int32_t* splits_per_dim, double* out_lb, uint8_t* out_infeasible,
@@ -724,9 +749,10 @@ extern "C" ivb_status ivb_get_tuning(ivb_problem* p, int32_t* block_threads, int
 }
 
 extern "C" ivb_status ivb_get_specialization(ivb_problem* p, int32_t* active, int32_t* registers,
-                                             int32_t* local_bytes, double* compile_seconds) {
+                                             int32_t* local_bytes, double* compile_seconds, int32_t* emulate) {
     if (!p) return fail(nullptr, IVB_EINVAL, "problem handle is NULL");
     if (active) *active = use_jit(p) ? 1 : 0;
+    if (emulate) *emulate = use_jit(p) ? p->jit.emulate : 0;
     if (registers) *registers = p->jit.regs;
     if (local_bytes) *local_bytes = p->jit.local_bytes;
     if (compile_seconds) *compile_seconds = p->jit.compile_seconds;
@@ -746,7 +772,7 @@ extern "C" ivb_status ivb_specialize_compile(const ivb_tape* tape, int32_t grad_
     e = compile_tape(tape, P, ins, rins, consts);
     if (!e.empty()) return fail(nullptr, IVB_ENOTSUP, e);
     const int mode = grad_mode == IVB_GRAD_ADJOINT ? KM_ADJ_REDUCE : KM_FWD_REDUCE;
-    const std::string src = jit_source(P, ins, rins, consts, mode, kJitBlockMax, kJitMinBlocks);
+    const std::string src = jit_source(P, ins, rins, consts, mode, kJitBlockMax, kJitMinBlocks, kJitDefaultEmulate);
     std::vector<char> cubin;
     std::string tables;
     int regs = 0, spill = 0;
@@ -760,9 +786,10 @@ extern "C" ivb_status ivb_specialize_compile(const ivb_tape* tape, int32_t grad_
 extern "C" ivb_status ivb_eval_op(int32_t opcode, int64_t n, const double* x, const double* y, double* r,
                                   void* cuda_stream) {
     if (n < 0 || !x || !r) return fail(nullptr, IVB_EINVAL, "ivb_eval_op: x and r are required");
-    const bool binary = opcode == IVB_OP_ADD || opcode == IVB_OP_SUB || opcode == IVB_OP_MUL || opcode == IVB_OP_DIV;
+    const bool binary = opcode == IVB_OP_ADD || opcode == IVB_OP_SUB || opcode == IVB_OP_MUL || opcode == IVB_OP_DIV ||
+                        opcode == IVB_EVAL_EMU_ADD || opcode == IVB_EVAL_EMU_SUB || opcode == IVB_EVAL_EMU_MUL;
     const bool unary = opcode == IVB_OP_SQR || opcode == IVB_OP_SQRT || opcode == IVB_OP_EXP || opcode == IVB_OP_LOG ||
-                       opcode == IVB_OP_NEG || opcode == IVB_EVAL_RECIP;
+                       opcode == IVB_OP_NEG || opcode == IVB_EVAL_RECIP || opcode == IVB_EVAL_EMU_SQR;
     if (!binary && !unary) return fail(nullptr, IVB_EINVAL, "ivb_eval_op: unknown opcode");
     if (binary && !y) return fail(nullptr, IVB_EINVAL, "ivb_eval_op: binary operation needs y");
     if (n == 0) return IVB_OK;

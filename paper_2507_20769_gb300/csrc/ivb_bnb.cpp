@@ -2,11 +2,16 @@
 // with GPU Subdomain Lower Bounding as the lower-bounding solver.
 //
 // Each iteration pops up to `batch` open nodes of lowest lower bound, bisects
-// each along the dimension of largest width relative to the root box, and
-// bounds all children in ONE ivb_bound_nodes_ex call (one persistent launch
-// when the problem is batched; one launch per child otherwise). The incumbent
-// comes from the rigorous centre-point upper bounds of the children (the
-// paper's local-solver upper bounding is replaced by these certified values).
+// each along the dimension of largest width relative to the root box,
+// optionally tightens every child by constraint propagation on the host
+// (dropping children proven empty), and bounds all children in ONE call of
+// the bounding path (one persistent launch when the problem is batched; one
+// launch per child otherwise). The incumbent comes from the rigorous
+// centre-point upper bounds of the children and from a descent-corner point
+// evaluated on the host (the paper's local-solver upper bounding is replaced
+// by these certified values). With `overlap`, the next batch is selected and
+// enqueued before the batch in flight is absorbed, so host work runs while
+// the GPU bounds.
 // Children that are infeasible or have lb >= UB - max(eps_abs, eps_rel |UB|)
 // are dropped. The run stops when UB - min(open lb) <= that tolerance, the
 // heap empties, or a node / time limit is reached; the reported lower bound
@@ -16,10 +21,16 @@
 #include <cmath>
 #include <cstring>
 #include <queue>
+#include <string>
 #include <vector>
 
 #include "../../include/ivb.h"
+#include "ivb_host.h"
 #include "ivb_problem.h"
+
+namespace ivb {
+std::string validate_tape(const ivb_tape* t);
+}
 
 namespace {
 
@@ -29,6 +40,20 @@ struct Node {
 };
 struct Cmp {
     bool operator()(const Node* a, const Node* b) const { return a->lb > b->lb; }
+};
+
+// one batch of children on its way through the bounding kernel: boxes and
+// splits staged on the host, results in pinned buffers, an event when done
+struct Batch {
+    std::vector<Node*> kids;
+    std::vector<double> boxes;
+    std::vector<int32_t> splits;
+    double* lb = nullptr;
+    double* ub = nullptr;
+    uint8_t* inf = nullptr;
+    cudaEvent_t done = nullptr;
+    double parent_lb = INFINITY;   // smallest lower bound of the parents (open while in flight)
+    bool in_flight = false;
 };
 
 }  // namespace
@@ -44,13 +69,34 @@ extern "C" void ivb_bnb_options_default(ivb_bnb_options* o) {
     o->max_nodes = 0;
     o->time_limit = 0.0;
     o->corner_ub = 1;
+    o->propagate = 0;
+    o->overlap = 0;
+}
+
+extern "C" ivb_status ivb_propagate(const ivb_tape* tape, int32_t n_boxes, const double* boxes, double ub,
+                                    int32_t passes, double* boxes_out, uint8_t* infeasible) {
+    if (!boxes || !boxes_out || !infeasible || n_boxes < 0 || passes < 0) return IVB_EINVAL;
+    if (!ivb::validate_tape(tape).empty()) return IVB_ETAPE;
+    ivb::HostTape H;
+    ivb::host_tape(tape, H);
+    const int n = H.n;
+    for (int k = 0; k < n_boxes; ++k) {
+        double* b = boxes_out + (size_t)k * 2 * n;
+        if (b != boxes + (size_t)k * 2 * n) std::memcpy(b, boxes + (size_t)k * 2 * n, 2 * n * sizeof(double));
+        infeasible[k] = (uint8_t)ivb::host_propagate(H, b, ub, passes);
+    }
+    return IVB_OK;
 }
 
 extern "C" ivb_status ivb_bnb_solve(ivb_problem* p, int32_t n, const double* root, const ivb_bnb_options* o,
-                                    ivb_bnb_result* res, void* stream) {
-    if (!p || !root || !o || !res || n < 1 || n > IVB_MAX_VARS) return IVB_EINVAL;
-    if (o->batch < 1 || (o->split_mode == 0 && !o->splits) || (o->split_mode > 0 && o->target < 1))
+                                    ivb_bnb_result* res, void* stream_) {
+    if (!p || !root || !o || !res || n < 1 || n > IVB_MAX_VARS || n != p->n) return IVB_EINVAL;
+    if (o->batch < 1 || (o->split_mode == 0 && !o->splits) || (o->split_mode > 0 && o->target < 1) ||
+        o->propagate < 0)
         return IVB_EINVAL;
+    cudaStream_t stream = (cudaStream_t)stream_;
+    const ivb::HostTape& H = p->host;
+    const int grad_mode = p->opt.grad_mode;
     using clk = std::chrono::steady_clock;
     const auto t0 = clk::now();
     auto elapsed = [&]() { return std::chrono::duration<double>(clk::now() - t0).count(); };
@@ -59,91 +105,96 @@ extern "C" ivb_status ivb_bnb_solve(ivb_problem* p, int32_t n, const double* roo
     std::priority_queue<Node*, std::vector<Node*>, Cmp> heap;
     double UB = INFINITY, lb_pruned = INFINITY;
     int64_t iters = 0, bounded = 0, subs = 0;
-    const int cap = 2 * o->batch;
-    std::vector<double> boxes((size_t)cap * n * 2), lb(cap), ub(cap);
-    std::vector<int32_t> splits((size_t)cap * n);
-    std::vector<uint8_t> inf(cap);
-    std::vector<Node*> kids;
+    const int cap = std::max(2 * o->batch, 1);
+    if (cap > p->max_nodes) return IVB_EINVAL;
 
-    auto set_splits = [&](const double* box, int32_t* sp) -> ivb_status {
-        if (o->split_mode == 0) { std::memcpy(sp, o->splits, n * sizeof(int32_t)); return IVB_OK; }
-        return ivb_pick_splits(n, box, ref.data(), o->target, o->split_mode - 1, sp);
+    Batch bat[2];
+    ivb_status st = IVB_OK;
+    for (Batch& b : bat) {
+        b.boxes.resize((size_t)cap * n * 2);
+        b.splits.resize((size_t)cap * n);
+        if (cudaMallocHost(&b.lb, cap * sizeof(double)) != cudaSuccess ||
+            cudaMallocHost(&b.ub, cap * sizeof(double)) != cudaSuccess ||
+            cudaMallocHost(&b.inf, cap) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) != cudaSuccess)
+            st = IVB_ENOMEM;
+    }
+    auto release = [&]() {
+        for (Batch& b : bat) {
+            if (b.in_flight && b.done) cudaEventSynchronize(b.done);
+            for (Node* k : b.kids) delete k;
+            b.kids.clear();
+            if (b.lb) cudaFreeHost(b.lb);
+            if (b.ub) cudaFreeHost(b.ub);
+            if (b.inf) cudaFreeHost(b.inf);
+            if (b.done) cudaEventDestroy(b.done);
+        }
+        while (!heap.empty()) { delete heap.top(); heap.pop(); }
     };
-    auto bound = [&](int cnt) -> ivb_status {
+    if (st) { release(); return st; }
+
+    auto tol_of = [&](double ub) { return std::max(o->eps_abs, o->eps_rel * std::fabs(ub)); };
+    // constraint propagation of a child against the incumbent; false: drop it
+    auto keep = [&](Node* k) {
+        return o->propagate == 0 || ivb::host_propagate(H, k->box.data(), UB, o->propagate) == 0;
+    };
+    // stage and enqueue a batch; its results arrive in the pinned buffers
+    auto launch = [&](Batch& b) -> ivb_status {
+        const int cnt = (int)b.kids.size();
         for (int k = 0; k < cnt; ++k) {
-            std::memcpy(&boxes[(size_t)k * n * 2], kids[k]->box.data(), n * 2 * sizeof(double));
-            ivb_status st = set_splits(kids[k]->box.data(), &splits[(size_t)k * n]);
-            if (st) return st;
+            std::memcpy(&b.boxes[(size_t)k * n * 2], b.kids[k]->box.data(), n * 2 * sizeof(double));
+            int32_t* sp = &b.splits[(size_t)k * n];
+            if (o->split_mode == 0) std::memcpy(sp, o->splits, n * sizeof(int32_t));
+            else if (ivb_status e = ivb_pick_splits(n, b.kids[k]->box.data(), ref.data(), o->target,
+                                                    o->split_mode - 1, sp))
+                return e;
             int64_t s = 1;
-            for (int i = 0; i < n; ++i) s *= splits[(size_t)k * n + i];
+            for (int i = 0; i < n; ++i) s *= sp[i];
             subs += s;
         }
         bounded += cnt;
-        return ivb_bound_nodes_ex(p, cnt, boxes.data(), splits.data(), lb.data(), inf.data(), ub.data(), nullptr,
-                                  nullptr, stream);
+        ivb_status e = bound_nodes_enqueue(p, cnt, b.boxes.data(), b.splits.data(), b.lb, b.inf, b.ub, nullptr,
+                                           nullptr, stream);
+        if (e) return e;
+        if (cudaEventRecord(b.done, stream) != cudaSuccess) return IVB_ECUDA;
+        b.in_flight = true;
+        return IVB_OK;
     };
-    // rigorous value of the objective at a point, +inf unless certified feasible
-    const int n_out = p->n_out, obj = p->obj;
-    std::vector<double> ptbox(2 * n), Fv(2 * n_out), Fcv(2 * n_out), Gv((size_t)2 * n_out * n);
-    std::vector<int32_t> ones(n, 1);
-    auto point_value = [&](const double* x) -> double {
-        for (int i = 0; i < n; ++i) { ptbox[2 * i] = x[i]; ptbox[2 * i + 1] = x[i]; }
-        if (ivb_enclose(p, ptbox.data(), ones.data(), 0, 1, Fv.data(), Fcv.data(), nullptr, stream) != IVB_OK)
-            return INFINITY;
-        if (p->P.has_eq) return INFINITY;
-        for (int q = 0; q < n_out; ++q)
-            if (p->out_kind[q] == IVB_OUT_INEQ && !(Fcv[2 * q + 1] <= 0.0)) return INFINITY;
-        return Fcv[2 * obj + 1];
-    };
-    // descent corner of a box: the sign of the objective's gradient enclosure
-    // over the box picks lo or hi per dimension, the centre where it is unknown
-    std::vector<double> cpt(n), mpt(n);
-    auto corner_value = [&](const double* box) -> double {
-        if (ivb_enclose(p, box, ones.data(), 0, 1, Fv.data(), nullptr, Gv.data(), stream) != IVB_OK) return INFINITY;
-        const double* G = Gv.data() + (size_t)obj * n * 2;
-        for (int i = 0; i < n; ++i) {
-            const double lo = box[2 * i], hi = box[2 * i + 1], c = (lo + hi) * 0.5;
-            cpt[i] = G[2 * i] > 0.0 ? lo : (G[2 * i + 1] < 0.0 ? hi : c);
-            mpt[i] = (cpt[i] + c) * 0.5;
-        }
-        const double v = point_value(cpt.data());
-        if (v < INFINITY) return v;
-        return point_value(mpt.data());
-    };
-    auto absorb = [&](int cnt) {
+    // wait for a batch, update the incumbent, push or drop its children
+    auto absorb = [&](Batch& b) -> ivb_status {
+        if (cudaEventSynchronize(b.done) != cudaSuccess) return IVB_ECUDA;
+        b.in_flight = false;
+        const int cnt = (int)b.kids.size();
         int best = -1;
         for (int k = 0; k < cnt; ++k) {
-            if (ub[k] < UB) UB = ub[k];
-            if (best < 0 || ub[k] < ub[best]) best = k;
+            if (b.ub[k] < UB) UB = b.ub[k];
+            if (best < 0 || b.ub[k] < b.ub[best]) best = k;
         }
         if (o->corner_ub && best >= 0) {
-            const double v = corner_value(kids[best]->box.data());
+            const double v = ivb::host_corner_value(H, b.kids[best]->box.data(), grad_mode);
             if (v < UB) UB = v;
         }
         for (int k = 0; k < cnt; ++k) {
-            const double tol = std::max(o->eps_abs, o->eps_rel * std::fabs(UB));
-            if (!inf[k] && !(lb[k] >= UB - tol)) {
-                kids[k]->lb = lb[k];
-                heap.push(kids[k]);
+            const double tol = tol_of(UB);
+            if (!b.inf[k] && !(b.lb[k] >= UB - tol)) {
+                b.kids[k]->lb = b.lb[k];
+                heap.push(b.kids[k]);
             } else {
-                if (!inf[k] && lb[k] < lb_pruned) lb_pruned = lb[k];
-                delete kids[k];
+                if (!b.inf[k] && b.lb[k] < lb_pruned) lb_pruned = b.lb[k];
+                delete b.kids[k];
             }
         }
-        kids.clear();
+        b.kids.clear();
+        return IVB_OK;
     };
-
-    kids.push_back(new Node{0.0, std::vector<double>(root, root + 2 * n)});
-    ivb_status st = bound(1);
-    if (st) { for (Node* k : kids) delete k; return st; }
-    absorb(1);
-    int converged = 0;
-    for (;;) {
-        if (heap.empty()) { converged = 1; break; }
-        const double tol = std::max(o->eps_abs, o->eps_rel * std::fabs(UB));
-        if (UB - heap.top()->lb <= tol) { converged = 1; break; }
-        if ((o->max_nodes > 0 && bounded >= o->max_nodes) || (o->time_limit > 0 && elapsed() > o->time_limit)) break;
-        while (!heap.empty() && (int)kids.size() < cap) {
+    // pop up to `batch` parents of lowest lower bound and bisect each along
+    // the dimension of largest width relative to the root box
+    auto select = [&](Batch& b) {
+        b.kids.clear();
+        b.parent_lb = INFINITY;
+        const double tol = tol_of(UB);
+        int parents = 0;
+        while (!heap.empty() && parents < o->batch) {
             Node* nd = heap.top();
             heap.pop();
             if (nd->lb >= UB - tol) {
@@ -152,6 +203,8 @@ extern "C" ivb_status ivb_bnb_solve(ivb_problem* p, int32_t n, const double* roo
                 continue;
             }
             ++iters;
+            ++parents;
+            b.parent_lb = std::min(b.parent_lb, nd->lb);
             int bi = 0;
             double bw = -1.0;
             for (int i = 0; i < n; ++i) {
@@ -163,14 +216,51 @@ extern "C" ivb_status ivb_bnb_solve(ivb_problem* p, int32_t n, const double* roo
             Node* l = new Node{0.0, nd->box};
             l->box[2 * bi + 1] = mid;
             nd->box[2 * bi] = mid;
-            kids.push_back(l);
-            kids.push_back(nd);
+            for (Node* k : {l, nd}) {
+                if (keep(k)) b.kids.push_back(k);
+                else delete k;
+            }
         }
-        if (kids.empty()) continue;
-        const int cnt = (int)kids.size();
-        st = bound(cnt);
-        if (st) { for (Node* k : kids) delete k; break; }
-        absorb(cnt);
+    };
+
+    int converged = 0;
+    {
+        Node* r = new Node{0.0, std::vector<double>(root, root + 2 * n)};
+        if (keep(r)) bat[0].kids.push_back(r);
+        else delete r;
+        if (!bat[0].kids.empty()) {
+            st = launch(bat[0]);
+            if (!st) st = absorb(bat[0]);
+        }
+    }
+    int cur = 0;   // overlap: the batch in flight, if any
+    while (!st) {
+        const double tol = tol_of(UB);
+        double open_lb = heap.empty() ? INFINITY : heap.top()->lb;
+        if (bat[cur].in_flight) open_lb = std::min(open_lb, bat[cur].parent_lb);
+        const bool idle = heap.empty() && !bat[cur].in_flight;
+        if (idle || UB - open_lb <= tol) {
+            converged = 1;
+            if (bat[cur].in_flight) st = absorb(bat[cur]);
+            break;
+        }
+        if ((o->max_nodes > 0 && bounded >= o->max_nodes) || (o->time_limit > 0 && elapsed() > o->time_limit)) {
+            if (bat[cur].in_flight) st = absorb(bat[cur]);
+            break;
+        }
+        if (!o->overlap) {
+            select(bat[0]);
+            if (bat[0].kids.empty()) continue;
+            st = launch(bat[0]);
+            if (!st) st = absorb(bat[0]);
+            continue;
+        }
+        // overlap: enqueue the next batch behind the one in flight, then absorb that one
+        Batch& next = bat[1 - cur];
+        select(next);
+        if (!next.kids.empty()) st = launch(next);
+        if (!st && bat[cur].in_flight) st = absorb(bat[cur]);
+        cur = 1 - cur;
     }
     double lbg = heap.empty() ? UB : heap.top()->lb;
     if (lb_pruned < lbg) lbg = lb_pruned;
@@ -182,6 +272,6 @@ extern "C" ivb_status ivb_bnb_solve(ivb_problem* p, int32_t n, const double* roo
     res->seconds = elapsed();
     res->converged = converged;
     res->open_nodes = (int64_t)heap.size();
-    while (!heap.empty()) { delete heap.top(); heap.pop(); }
+    release();
     return st;
 }

@@ -79,24 +79,59 @@ __device__ __forceinline__ double next_dn(double y) { return ineg(next_up(ineg(y
 }  // namespace ivb
 
 #include "ivb_fp64x.cuh"
+#include "ivb_emu.cuh"
+
+// Which endpoint operations run as the integer-pipe emulation of
+// ivb_emu.cuh (bit-identical to the FP64 instructions): bit 0 upper ends of
+// products, bit 1 lower ends of products, bit 2 upper ends of sums and
+// differences, bit 3 lower ends. The precompiled kernels use none; the
+// tape-specialised kernels are compiled with the policy of their problem.
+#ifndef IVB_EMU
+#define IVB_EMU 0
+#endif
 
 namespace ivb {
 
 // ---------------------------------------------------------------- endpoints
-__device__ __forceinline__ double add_dn(double x, double y) { return __dadd_rd(x, y); }
-__device__ __forceinline__ double add_up(double x, double y) { return __dadd_ru(x, y); }
-__device__ __forceinline__ double sub_dn(double x, double y) { return __dsub_rd(x, y); }
-__device__ __forceinline__ double sub_up(double x, double y) { return __dsub_ru(x, y); }
+// templates on the emulation policy E; the plain names use IVB_EMU
+template <int E> __device__ __forceinline__ double add_dn_t(double x, double y) {
+    return (E & 8) ? add_rd_emu(x, y) : __dadd_rd(x, y);
+}
+template <int E> __device__ __forceinline__ double add_up_t(double x, double y) {
+    return (E & 4) ? add_ru_emu(x, y) : __dadd_ru(x, y);
+}
+template <int E> __device__ __forceinline__ double sub_dn_t(double x, double y) {
+    return (E & 8) ? add_rd_emu(x, ineg(y)) : __dsub_rd(x, y);
+}
+template <int E> __device__ __forceinline__ double sub_up_t(double x, double y) {
+    return (E & 4) ? add_ru_emu(x, ineg(y)) : __dsub_ru(x, y);
+}
 
 // products with 0 * inf = 0 (interval factors are sets of reals)
-__device__ __forceinline__ double prod_dn(double x, double y) {
+__device__ __forceinline__ double prod_dir_emu(double x, double y, bool up) {
+    const bool z = is0(x) || is0(y);
+    bool ok;
+    double p = mul_dir_emu_fast(x, y, up, ok);
+    if (!ok && !z) p = up ? mul_ru_hw(x, y) : mul_rd_hw(x, y);
+    return z ? 0.0 : p;
+}
+template <int E> __device__ __forceinline__ double prod_dn_t(double x, double y) {
+    if (E & 2) return prod_dir_emu(x, y, false);
     double p = __dmul_rd(x, y);
     return (is0(x) || is0(y)) ? 0.0 : p;
 }
-__device__ __forceinline__ double prod_up(double x, double y) {
+template <int E> __device__ __forceinline__ double prod_up_t(double x, double y) {
+    if (E & 1) return prod_dir_emu(x, y, true);
     double p = __dmul_ru(x, y);
     return (is0(x) || is0(y)) ? 0.0 : p;
 }
+
+__device__ __forceinline__ double add_dn(double x, double y) { return add_dn_t<IVB_EMU>(x, y); }
+__device__ __forceinline__ double add_up(double x, double y) { return add_up_t<IVB_EMU>(x, y); }
+__device__ __forceinline__ double sub_dn(double x, double y) { return sub_dn_t<IVB_EMU>(x, y); }
+__device__ __forceinline__ double sub_up(double x, double y) { return sub_up_t<IVB_EMU>(x, y); }
+__device__ __forceinline__ double prod_dn(double x, double y) { return prod_dn_t<IVB_EMU>(x, y); }
+__device__ __forceinline__ double prod_up(double x, double y) { return prod_up_t<IVB_EMU>(x, y); }
 
 // ---------------------------------------------------------------- intervals
 __device__ __forceinline__ iv mk(double lo, double hi) { iv r; r.lo = lo; r.hi = hi; return r; }
@@ -105,8 +140,14 @@ __device__ __forceinline__ iv zero() { return mk(0.0, 0.0); }
 __device__ __forceinline__ iv one() { return mk(1.0, 1.0); }
 __device__ __forceinline__ bool has_inf(iv x) { return isinf_(x.lo) || isinf_(x.hi); }
 
-__device__ __forceinline__ iv iv_add(iv x, iv y) { return mk(add_dn(x.lo, y.lo), add_up(x.hi, y.hi)); }
-__device__ __forceinline__ iv iv_sub(iv x, iv y) { return mk(sub_dn(x.lo, y.hi), sub_up(x.hi, y.lo)); }
+template <int E> __device__ __forceinline__ iv iv_add_t(iv x, iv y) {
+    return mk(add_dn_t<E>(x.lo, y.lo), add_up_t<E>(x.hi, y.hi));
+}
+template <int E> __device__ __forceinline__ iv iv_sub_t(iv x, iv y) {
+    return mk(sub_dn_t<E>(x.lo, y.hi), sub_up_t<E>(x.hi, y.lo));
+}
+__device__ __forceinline__ iv iv_add(iv x, iv y) { return iv_add_t<IVB_EMU>(x, y); }
+__device__ __forceinline__ iv iv_sub(iv x, iv y) { return iv_sub_t<IVB_EMU>(x, y); }
 __device__ __forceinline__ iv iv_neg(iv x) { return mk(ineg(x.hi), ineg(x.lo)); }
 
 // product: sign-case choice of the endpoint pairs that realise min and max of
@@ -115,7 +156,7 @@ __device__ __forceinline__ iv iv_neg(iv x) { return mk(ineg(x.hi), ineg(x.lo)); 
 // the same two directed multiplies; lanes where both factors straddle 0 need a
 // second pair, issued only when some lane of the warp needs it (warp-uniform
 // branch: no FP64 instruction runs with idle lanes for the common case).
-__device__ __forceinline__ iv iv_mul(iv x, iv y) {
+template <int E> __device__ __forceinline__ iv iv_mul_t(iv x, iv y) {
     const bool xP = ge0(x.lo), xN = !xP && le0(x.hi), xM = !xP && !xN;
     const bool yP = ge0(y.lo), yN = !yP && le0(y.hi), yM = !yP && !yN;
     const bool mm = xM && yM;
@@ -127,15 +168,16 @@ __device__ __forceinline__ iv iv_mul(iv x, iv y) {
     const double ly = mm ? y.hi : ((xP || (xM && yN)) ? y.lo : y.hi);
     const double ux = mm ? x.lo : ((xP ? !yN : yP) ? x.hi : x.lo);
     const double uy = mm ? y.lo : ((xP || (xM && yP)) ? y.hi : y.lo);
-    double lo = prod_dn(lx, ly), hi = prod_up(ux, uy);
+    double lo = prod_dn_t<E>(lx, ly), hi = prod_up_t<E>(ux, uy);
     if (__any_sync(__activemask(), mm)) {
-        const double lo2 = prod_dn(mm ? x.hi : lx, mm ? y.lo : ly);
-        const double hi2 = prod_up(mm ? x.hi : ux, mm ? y.hi : uy);
+        const double lo2 = prod_dn_t<E>(mm ? x.hi : lx, mm ? y.lo : ly);
+        const double hi2 = prod_up_t<E>(mm ? x.hi : ux, mm ? y.hi : uy);
         lo = imin(lo, lo2);
         hi = imax(hi, hi2);
     }
     return mk(lo, hi);
 }
+__device__ __forceinline__ iv iv_mul(iv x, iv y) { return iv_mul_t<IVB_EMU>(x, y); }
 
 // 2*x rounded toward -inf / +inf: exact (an exponent increment on the integer
 // pipe, or a shift for zero and subnormals) unless |x| >= 2^1023, where the
@@ -151,13 +193,14 @@ __device__ __forceinline__ iv iv_twice(iv x) { return mk(twice_dir(x.lo, false),
 
 // square: [a^2, b^2] with b = max(|lo|, |hi|) and a = min(|lo|, |hi|), or
 // a = 0 when the interval straddles 0 -- two directed multiplies, no branch
-__device__ __forceinline__ iv iv_sqr(iv x) {
+template <int E> __device__ __forceinline__ iv iv_sqr_t(iv x) {
     const long long ml = bits(x.lo) & 0x7FFFFFFFFFFFFFFFLL, mh = bits(x.hi) & 0x7FFFFFFFFFFFFFFFLL;
     const bool straddle = !ge0(x.lo) && !le0(x.hi);
     const double big = from_bits(ml > mh ? ml : mh);
     const double small = straddle ? 0.0 : from_bits(ml > mh ? mh : ml);
-    return mk(prod_dn(small, small), prod_up(big, big));
+    return mk(prod_dn_t<E>(small, small), prod_up_t<E>(big, big));
 }
+__device__ __forceinline__ iv iv_sqr(iv x) { return iv_sqr_t<IVB_EMU>(x); }
 
 // reciprocal of an interval without 0 (ENTIRE otherwise)
 __device__ __forceinline__ iv iv_recip(iv y) {

@@ -252,8 +252,9 @@ struct Gen {
         line(ind, "}");
     }
 
-    std::string kernel(int mode, int block_max, int min_blocks) {
+    std::string kernel(int mode, int block_max, int min_blocks, int emulate) {
         out.clear();
+        line(0, "#define IVB_EMU " + S(emulate));
         line(0, "typedef signed char int8_t; typedef unsigned char uint8_t;");
         line(0, "typedef short int16_t; typedef unsigned short uint16_t;");
         line(0, "typedef int int32_t; typedef unsigned int uint32_t;");
@@ -340,9 +341,9 @@ struct Gen {
 }  // namespace
 
 std::string jit_source(const HostProgram& P, const std::vector<Ins>& ins, const std::vector<RIns>& rins,
-                       const std::vector<double>& consts, int mode, int block_max, int min_blocks) {
+                       const std::vector<double>& consts, int mode, int block_max, int min_blocks, int emulate) {
     Gen g{P, ins.data(), rins.data(), consts.data(), P.n_vars, P.n_out, {}};
-    return g.kernel(mode, block_max, min_blocks);
+    return g.kernel(mode, block_max, min_blocks, emulate);
 }
 
 std::string jit_compile(const std::string& src, std::vector<char>& cubin, std::string& tables_name, double* seconds,

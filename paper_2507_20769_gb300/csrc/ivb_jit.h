@@ -15,19 +15,26 @@ namespace ivb {
 // most 128 registers per thread; specialize = -1 compiles tapes of at most
 // kJitAutoMaxOps interval operations per subdomain
 constexpr int kJitBlockMax = 256, kJitMinBlocks = 2, kJitAutoMaxOps = 4096;
+// endpoint operations emulated on the integer pipes by default (ivb_iv.cuh
+// policy bits): none -- on configuration 2 no policy beat the FP64 pipe alone
+// by more than the noise (the kernel runs at its 128-register cap with 16
+// warps per SM and long dependency chains, so the emulation's latency, not
+// the FP64 pipe, ends up on the critical path)
+constexpr int kJitDefaultEmulate = 0;
 
 struct JitKernel {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kern = nullptr;
     int mode = -1;             // KM_FWD_REDUCE or KM_ADJ_REDUCE
     int block_max = 0;         // __launch_bounds__ of the generated kernel
+    int emulate = 0;           // emulation policy compiled in
     int regs = 0, local_bytes = 0, max_threads = 0;
     double compile_seconds = 0.0;
 };
 
 // CUDA C++ of the reduce-mode bounding kernel for this program
 std::string jit_source(const HostProgram& P, const std::vector<Ins>& ins, const std::vector<RIns>& rins,
-                       const std::vector<double>& consts, int mode, int block_max, int min_blocks);
+                       const std::vector<double>& consts, int mode, int block_max, int min_blocks, int emulate);
 // NVRTC for sm_103a; "" on success, else the compiler's message. With
 // `registers` / `spill_bytes` non-NULL, ptxas reports them (parsed from its log).
 std::string jit_compile(const std::string& src, std::vector<char>& cubin, std::string& tables_name, double* seconds,

@@ -474,13 +474,26 @@ __global__ void __launch_bounds__(256) k_point_grad(const ProgDesc* __restrict__
 }
 
 // ------------------------------------------------------------ test hook
-// opcode: tape opcodes of the interval operations, or 100 for the reciprocal
+// opcode: tape opcodes of the interval operations, 100 for the reciprocal,
+// 101..104 for +, -, *, sqr with every endpoint operation emulated on the
+// integer pipes (policy 15 of ivb_iv.cuh)
+__device__ __forceinline__ iv eval_hook(int opcode, iv X, iv Y) {
+    switch (opcode) {
+    case 100: return iv_recip(X);
+    case 101: return iv_add_t<15>(X, Y);
+    case 102: return iv_sub_t<15>(X, Y);
+    case 103: return iv_mul_t<15>(X, Y);
+    case 104: return iv_sqr_t<15>(X);
+    }
+    return eval_value((uint32_t)opcode, X, Y);
+}
+
 __global__ void k_eval_op(int opcode, long long n, const double* __restrict__ x, const double* __restrict__ y,
                           double* r) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const iv X = mk(x[2 * i], x[2 * i + 1]);
         const iv Y = y ? mk(y[2 * i], y[2 * i + 1]) : X;
-        const iv R = opcode == 100 ? iv_recip(X) : eval_value((uint32_t)opcode, X, Y);
+        const iv R = eval_hook(opcode, X, Y);
         r[2 * i] = R.lo;
         r[2 * i + 1] = R.hi;
     }
@@ -502,6 +515,9 @@ __global__ void k_own_probe(double* out, double seed, int iters) {
     const double y = seed + threadIdx.x * 1e-12;
     for (int j = 0; j < 8; ++j) x[j] = 1.5 + j * 1e-3 + threadIdx.x * 1e-9;
     for (int i = 0; i < iters; ++i) {
+        // factors and addends that keep the multiply / add chains near 1.5
+        const double f = (i & 1) ? 1.0000001192092896 : 0.99999988079071045;
+        const double d = (i & 1) ? 0.0009765625 : -0.0009765625;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             if (W == 0) x[j] = rcp_dir_pos(x[j], false);
@@ -509,6 +525,11 @@ __global__ void k_own_probe(double* out, double seed, int iters) {
             if (W == 2) x[j] = sqrt_dir(x[j] * 3.1, false);   // one multiply keeps x off powers of two
             if (W == 3) x[j] = exp_dir(-x[j], false);
             if (W == 4) x[j] = __dadd_rn(log_dir(x[j], false), 2.0);
+            // integer-pipe emulation (ivb_emu.cuh) alone, and beside the FP64 pipe (half the chains each)
+            if (W == 5) x[j] = mul_ru_emu(x[j], f);
+            if (W == 6) x[j] = (j & 1) ? mul_ru_emu(x[j], f) : __dmul_ru(x[j], f);
+            if (W == 7) x[j] = add_ru_emu(x[j], d);
+            if (W == 8) x[j] = (j & 1) ? add_ru_emu(x[j], d) : __dadd_ru(x[j], d);
         }
     }
     double acc = 0.0;
@@ -541,7 +562,11 @@ cudaError_t run_own_probe(int which, double* out, int grid, int block, int iters
     case 1: return own_probe_run<1>(out, grid, block, iters, ms);
     case 2: return own_probe_run<2>(out, grid, block, iters, ms);
     case 3: return own_probe_run<3>(out, grid, block, iters, ms);
-    default: return own_probe_run<4>(out, grid, block, iters, ms);
+    case 4: return own_probe_run<4>(out, grid, block, iters, ms);
+    case 5: return own_probe_run<5>(out, grid, block, iters, ms);
+    case 6: return own_probe_run<6>(out, grid, block, iters, ms);
+    case 7: return own_probe_run<7>(out, grid, block, iters, ms);
+    default: return own_probe_run<8>(out, grid, block, iters, ms);
     }
 }
 

@@ -59,7 +59,7 @@ cudaError_t run(double* out, int grid, int block, int iters, float* ms) {
 }  // namespace
 
 extern "C" ivb_status ivb_fp64_probe(int32_t which, int32_t iters, double* lane_ops_per_s) {
-    if (!lane_ops_per_s || iters < 1 || which < 0 || which > IVB_PROBE_OWN_LOG) return IVB_EINVAL;
+    if (!lane_ops_per_s || iters < 1 || which < 0 || which > IVB_PROBE_MIXED_ADD) return IVB_EINVAL;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return IVB_ECUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return IVB_ECUDA;
@@ -70,7 +70,8 @@ extern "C" ivb_status ivb_fp64_probe(int32_t which, int32_t iters, double* lane_
     cudaError_t e;
     switch (which) {
     case IVB_PROBE_OWN_RCP: case IVB_PROBE_OWN_DIV: case IVB_PROBE_OWN_SQRT: case IVB_PROBE_OWN_EXP:
-    case IVB_PROBE_OWN_LOG:
+    case IVB_PROBE_OWN_LOG: case IVB_PROBE_EMU_MUL: case IVB_PROBE_MIXED_MUL: case IVB_PROBE_EMU_ADD:
+    case IVB_PROBE_MIXED_ADD:
         e = ivb::run_own_probe(which - IVB_PROBE_OWN_RCP, out, grid, block, iters, &ms);
         break;
     case IVB_PROBE_DADD: e = run<IVB_PROBE_DADD>(out, grid, block, iters, &ms); break;

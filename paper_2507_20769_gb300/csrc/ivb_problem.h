@@ -6,6 +6,7 @@
 #include <string>
 
 #include "../../include/ivb.h"
+#include "ivb_host.h"
 #include "ivb_internal.h"
 #include "ivb_jit.h"
 #include "ivb_kernels.h"
@@ -13,6 +14,7 @@
 struct ivb_problem {
     ivb_options opt{};
     ivb::HostProgram P{};
+    ivb::HostTape host;       // the tape for host-side evaluation (B&B)
     int n = 0, n_out = 0, obj = 0;
     uint8_t out_kind[64]{};
     // program on the device
@@ -50,3 +52,9 @@ struct ivb_problem {
     ivb::JitKernel jit;
     std::string err;
 };
+
+// ivb_bound_nodes_ex without the final wait: results reach host buffers
+// asynchronously (pinned buffers for true overlap); the caller orders on `s`
+ivb_status bound_nodes_enqueue(ivb_problem* p, int32_t n_nodes, const double* boxes, const int32_t* splits,
+                               double* out_lb, uint8_t* out_inf, double* out_ub, double* out_minlo,
+                               double* out_maxhi, cudaStream_t s);

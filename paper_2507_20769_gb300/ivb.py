@@ -35,7 +35,8 @@ class ivb_options(ctypes.Structure):
     _fields_ = [("grad_mode", ctypes.c_int32), ("form", ctypes.c_int32), ("filter", ctypes.c_int32),
                 ("batched", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("max_nodes", ctypes.c_int32), ("frame_in_shared", ctypes.c_int32), ("specialize", ctypes.c_int32)]
+                ("max_nodes", ctypes.c_int32), ("frame_in_shared", ctypes.c_int32), ("specialize", ctypes.c_int32),
+                ("emulate", ctypes.c_int32)]
 
 
 class ivb_tape(ctypes.Structure):
@@ -46,7 +47,8 @@ class ivb_tape(ctypes.Structure):
 class ivb_bnb_options(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int32), ("split_mode", ctypes.c_int32), ("splits", ctypes.c_void_p),
                 ("target", ctypes.c_int64), ("eps_abs", ctypes.c_double), ("eps_rel", ctypes.c_double),
-                ("max_nodes", ctypes.c_int64), ("time_limit", ctypes.c_double), ("corner_ub", ctypes.c_int32)]
+                ("max_nodes", ctypes.c_int64), ("time_limit", ctypes.c_double), ("corner_ub", ctypes.c_int32),
+                ("propagate", ctypes.c_int32), ("overlap", ctypes.c_int32)]
 
 
 class ivb_bnb_result(ctypes.Structure):
@@ -91,11 +93,13 @@ def lib() -> ctypes.CDLL:
         L.ivb_fp64_probe.argtypes = [I32, I32, P]
         L.ivb_bnb_options_default.argtypes = [P]
         L.ivb_bnb_solve.argtypes = [P, I32, P, P, P, P]
-        L.ivb_get_specialization.argtypes = [P, P, P, P, P]
+        L.ivb_get_specialization.argtypes = [P, P, P, P, P, P]
+        L.ivb_propagate.argtypes = [P, I32, P, D, I32, P, P]
         L.ivb_specialize_compile.argtypes = [P, I32, P, P, P]
         for f in ("ivb_create_problem", "ivb_bound_nodes", "ivb_bound_nodes_ex", "ivb_enclose", "ivb_point_grad",
                   "ivb_pick_splits", "ivb_get_tuning", "ivb_bnb_solve", "ivb_op_counts", "ivb_fp64_probe",
-                  "ivb_bound_nodes_noalloc", "ivb_eval_op", "ivb_get_specialization", "ivb_specialize_compile"):
+                  "ivb_bound_nodes_noalloc", "ivb_eval_op", "ivb_get_specialization", "ivb_specialize_compile",
+                  "ivb_propagate"):
             getattr(L, f).restype = I32
         _lib = L
     return _lib
@@ -182,7 +186,8 @@ def ivb_pick_splits(box, target: int, strategy="adaptive", ref_widths=None) -> n
 
 CNT_NAMES = ("addsub", "mul", "div", "rcp", "sqrt", "exp", "log", "rn")
 PROBE = {"dadd": 0, "dmul": 1, "dfma": 2, "ddiv": 3, "drcp": 4, "dsqrt": 5, "exp": 6, "log": 7,
-         "own_rcp": 8, "own_div": 9, "own_sqrt": 10, "own_exp": 11, "own_log": 12}
+         "own_rcp": 8, "own_div": 9, "own_sqrt": 10, "own_exp": 11, "own_log": 12,
+         "emu_mul": 13, "mixed_mul": 14, "emu_add": 15, "mixed_add": 16}
 
 
 def ivb_fp64_probe(which: str, iters: int = 1024) -> float:
@@ -193,6 +198,7 @@ def ivb_fp64_probe(which: str, iters: int = 1024) -> float:
 
 
 IVB_EVAL_RECIP = 100
+IVB_EVAL_EMU_ADD, IVB_EVAL_EMU_SUB, IVB_EVAL_EMU_MUL, IVB_EVAL_EMU_SQR = 101, 102, 103, 104
 
 
 def ivb_eval_op(opcode: int, x, y=None):
@@ -221,6 +227,27 @@ def ivb_specialize_compile(tape, grad_mode="adjoint") -> dict:
     _check(lib().ivb_specialize_compile(ctypes.byref(t), g, ctypes.byref(regs), ctypes.byref(spill),
                                         ctypes.byref(secs)))
     return {"registers": regs.value, "spill_bytes": spill.value, "seconds": secs.value}
+
+
+def _c_tape(tape):
+    recs = tape.records()
+    oi = np.ascontiguousarray(tape.out_idx, dtype=np.int32)
+    ok = np.ascontiguousarray(tape.out_kind, dtype=np.uint8)
+    t = ivb_tape(int(tape.n_vars), int(recs.shape[0]), int(oi.shape[0]), recs.ctypes.data, oi.ctypes.data,
+                 ok.ctypes.data)
+    return t, (recs, oi, ok)
+
+
+def ivb_propagate(tape, boxes, ub=float("inf"), passes=4):
+    """constraint propagation on the host (no GPU): tightened boxes
+    [k, n, 2] and infeasible flags [k]"""
+    bx = np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1, int(tape.n_vars), 2)
+    out = np.empty_like(bx)
+    inf = np.empty(bx.shape[0], dtype=np.uint8)
+    t, keep = _c_tape(tape)
+    _check(lib().ivb_propagate(ctypes.byref(t), bx.shape[0], _ptr(bx), float(ub), int(passes), _ptr(out),
+                               _ptr(inf)))
+    return out, inf.astype(bool)
 
 
 def ivb_last_error(problem=None) -> str:
@@ -331,7 +358,7 @@ class Problem:
         return f, g
 
     def ivb_bnb_solve(self, root, splits=None, target=0, strategy="adaptive", batch=1, eps_abs=0.0,
-                      eps_rel=1e-3, max_nodes=0, time_limit=0.0, corner_ub=1):
+                      eps_rel=1e-3, max_nodes=0, time_limit=0.0, corner_ub=1, propagate=0, overlap=0, stream=None):
         root = np.ascontiguousarray(root, dtype=np.float64)
         o = ivb_bnb_options()
         lib().ivb_bnb_options_default(ctypes.byref(o))
@@ -344,8 +371,9 @@ class Problem:
             o.target = int(target)
         o.batch, o.eps_abs, o.eps_rel = int(batch), float(eps_abs), float(eps_rel)
         o.max_nodes, o.time_limit, o.corner_ub = int(max_nodes), float(time_limit), int(corner_ub)
+        o.propagate, o.overlap = int(propagate), int(overlap)
         r = ivb_bnb_result()
-        _check(lib().ivb_bnb_solve(self._h, self.n_vars, _ptr(root), ctypes.byref(o), ctypes.byref(r), None),
+        _check(lib().ivb_bnb_solve(self._h, self.n_vars, _ptr(root), ctypes.byref(o), ctypes.byref(r), stream),
                self._h)
         return {"lb": r.lb, "ub": r.ub, "iterations": r.iterations, "nodes": r.nodes_bounded,
                 "subdomains": r.subdomains, "seconds": r.seconds, "converged": bool(r.converged),
@@ -358,10 +386,11 @@ class Problem:
                 "frame_in_shared": v[3].value}
 
     def ivb_get_specialization(self) -> dict:
-        a, r, lb, sec = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        a, r, lb, sec, em = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double(), ctypes.c_int32()
         _check(lib().ivb_get_specialization(self._h, ctypes.byref(a), ctypes.byref(r), ctypes.byref(lb),
-                                            ctypes.byref(sec)), self._h)
-        return {"active": bool(a.value), "registers": r.value, "local_bytes": lb.value, "compile_seconds": sec.value}
+                                            ctypes.byref(sec), ctypes.byref(em)), self._h)
+        return {"active": bool(a.value), "registers": r.value, "local_bytes": lb.value, "compile_seconds": sec.value,
+                "emulate": em.value}
 
     def ivb_op_counts(self) -> dict:
         c = (ctypes.c_int64 * 8)()

@@ -40,9 +40,9 @@ def test_library_exports_every_declared_function(lib):
 
 def test_struct_sizes_match_header(lib):
     assert W.IVB_OP_DTYPE.itemsize == 24
-    assert ctypes.sizeof(ivb.ivb_options) == 12 * 4
+    assert ctypes.sizeof(ivb.ivb_options) == 13 * 4
     o = ivb.ivb_options_default()
-    assert (o.grad_mode, o.form, o.batched, o.use_graph, o.max_nodes, o.specialize) == (1, 0, 1, 1, 4096, 0)
+    assert (o.grad_mode, o.form, o.batched, o.use_graph, o.max_nodes, o.specialize, o.emulate) == (1, 0, 1, 1, 4096, 0, -1)
 
 
 def _raw_create(tape_like):

@@ -1,7 +1,9 @@
 """The kernels' interval operations (through the C-ABI test hook ivb_eval_op)
 against the oracle's, on large sets of random and special operands:
 + - * / sqr sqrt and the reciprocal bit for bit (directed rounding is unique);
-exp and log contain the oracle's tight enclosure, each end within 4 ulps."""
+exp and log contain the oracle's tight enclosure, each end within 4 ulps;
++ - * sqr with the integer-pipe emulation of the endpoint operations bit for
+bit, signed zeros included."""
 from __future__ import annotations
 
 import numpy as np
@@ -135,3 +137,76 @@ def test_exp_log_contain_oracle_within_4_ulps(fn):
     assert np.all(ulps(R[fin, 0], Ro[fin, 0]) <= 4)
     fin = np.isfinite(Ro[:, 1]) & (Ro[:, 1] != 0)
     assert np.all(ulps(R[fin, 1], Ro[fin, 1]) <= 4)
+
+
+# ---------------------------------------- integer-pipe emulation (option emulate)
+
+def emulation_operands(rng, n):
+    """pairs aimed at the emulated add and multiply: every exponent difference
+    up to 70 with both signs (alignment, sticky bits, carries), near-cancelling
+    sums, all-ones and power-of-two significands (rounding carries into the
+    exponent), products and sums near overflow and underflow, subnormals,
+    zeros, infinities"""
+    def sig(k, kind):
+        m = rng.uniform(1.0, 2.0, k)
+        if kind == 1:
+            m = np.full(k, np.nextafter(2.0, 1.0))
+        elif kind == 2:
+            m = np.ones(k)
+        return m
+    xs, ys = [], []
+    # exponent differences 0..70, random signs and significand classes
+    k = n // 4
+    ex = rng.integers(-60, 60, k)
+    d = rng.integers(0, 71, k)
+    kx, ky = rng.integers(0, 3, k), rng.integers(0, 3, k)
+    x = np.ldexp(np.where(kx == 0, sig(k, 0), np.where(kx == 1, sig(k, 1), 1.0)), ex)
+    y = np.ldexp(np.where(ky == 0, sig(k, 0), np.where(ky == 1, sig(k, 1), 1.0)), ex - d)
+    xs.append(x * rng.choice([-1.0, 1.0], k))
+    ys.append(y * rng.choice([-1.0, 1.0], k))
+    # near cancellation: y = -x (1 + tiny), and y = -x exactly
+    x = np.ldexp(rng.uniform(1.0, 2.0, k), rng.integers(-100, 100, k))
+    rel = np.where(rng.random(k) < 0.1, 0.0, rng.choice([-1.0, 1.0], k) * 2.0 ** rng.uniform(-53, -2, k))
+    xs.append(x)
+    ys.append(-x * (1.0 + rel))
+    # near overflow / underflow of products and sums
+    e1 = rng.integers(-1022, 1024, k)
+    e2 = np.where(rng.random(k) < 0.5, 1023 - e1 + rng.integers(-2, 3, k), -1022 - e1 + rng.integers(-2, 3, k))
+    xs.append(np.ldexp(rng.uniform(1.0, 2.0, k), e1) * rng.choice([-1.0, 1.0], k))
+    ys.append(np.ldexp(rng.uniform(1.0, 2.0, k), np.clip(e2, -1074, 1023)) * rng.choice([-1.0, 1.0], k))
+    # full range, subnormals included
+    xs.append(random_doubles(rng, k, -1074, 1023))
+    ys.append(random_doubles(rng, k, -1074, 1023))
+    x, y = np.concatenate(xs), np.concatenate(ys)
+    s = np.concatenate([specials(), [np.inf, -np.inf]])
+    sx, sy = np.meshgrid(s, s)
+    x, y = np.concatenate([x, sx.ravel()]), np.concatenate([y, sy.ravel()])
+    return x, y
+
+
+def same_bits_or_nan(a, b):
+    return (a.view(np.int64) == b.view(np.int64)) | (np.isnan(a) & np.isnan(b))
+
+
+@pytest.mark.parametrize("name,opcode,emu", [("add", W.OP_ADD, ivb.IVB_EVAL_EMU_ADD), ("sub", W.OP_SUB, ivb.IVB_EVAL_EMU_SUB),
+                                             ("mul", W.OP_MUL, ivb.IVB_EVAL_EMU_MUL), ("sqr", W.OP_SQR, ivb.IVB_EVAL_EMU_SQR)])
+def test_emulated_ops_bit_exact(name, opcode, emu):
+    """+ - * sqr with every endpoint operation emulated on the integer pipes
+    equal the oracle's directed operations bit for bit (signed zeros
+    included), on points (single directed operations) and on intervals"""
+    rng = np.random.default_rng(1000 + opcode)
+    x, y = emulation_operands(rng, 1_600_000)
+    # points: [x, x] op [y, y] gives the directed operation at both ends
+    X, Y = np.stack([x, x], 1), np.stack([y, y], 1)
+    XI = intervals(rng, 400000, -1074, 1023)
+    YI = intervals(rng, 400000, -1074, 1023)
+    m = min(len(XI), len(YI))
+    X, Y = np.concatenate([X, XI[:m]]), np.concatenate([Y, YI[:m]])
+    unary = opcode == W.OP_SQR
+    R = gpu(emu, X, None if unary else Y)
+    Ro = oracle.iv_op(opcode, X, None if unary else Y)
+    bad = ~same_bits_or_nan(R, Ro).all(axis=1)
+    assert not bad.any(), (name, int(bad.sum()), X[bad][:3], Y[bad][:3], R[bad][:3], Ro[bad][:3])
+    # the hardware path gives the same bits
+    Rh = gpu(opcode, X, None if unary else Y)
+    assert same_bits_or_nan(R, Rh).all()

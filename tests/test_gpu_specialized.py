@@ -59,13 +59,16 @@ def bound_both(t, boxes, splits, **opts):
 
 @pytest.mark.parametrize("grad_mode", ["forward", "adjoint"])
 @pytest.mark.parametrize("path", ["graph", "nograph", "plain"])
-def test_specialized_bit_exact_rational_vs_oracle(grad_mode, path):
+@pytest.mark.parametrize("emulate", [0, 15])
+def test_specialized_bit_exact_rational_vs_oracle(grad_mode, path, emulate):
     """ragged batch (S from 1 to 216 per node, tiles crossing nodes), every
-    launch path: lb, infeasibility, centre upper bound and each output's hull
-    equal the oracle's bit for bit"""
+    launch path, endpoint operations on the FP64 pipe (0) or all emulated on
+    the integer pipes (15): lb, infeasibility, centre upper bound and each
+    output's hull equal the oracle's bit for bit"""
     t = rational_problem()
     boxes, splits = ragged_batch(t, 37, seed=11)
-    opts = dict(grad_mode=grad_mode, use_graph=int(path == "graph"), batched=int(path != "plain"), specialize=1)
+    opts = dict(grad_mode=grad_mode, use_graph=int(path == "graph"), batched=int(path != "plain"), specialize=1,
+                emulate=emulate)
     with ivb.Problem(t, **opts) as p:
         assert p.get_specialization()["active"]
         r = p.bound_nodes_ex(boxes, splits, want_hull=True)
@@ -79,11 +82,13 @@ def test_specialized_bit_exact_rational_vs_oracle(grad_mode, path):
 
 @pytest.mark.parametrize("grad_mode", ["forward", "adjoint"])
 @pytest.mark.parametrize("form", ["mvf", "nie", "mvf_nie"])
-def test_specialized_identical_to_interpreter_exp_log(grad_mode, form):
-    """configuration 1 (exp/log tape): all results bit-identical to the interpreter"""
+@pytest.mark.parametrize("emulate", [-1, 0, 5, 10, 15])
+def test_specialized_identical_to_interpreter_exp_log(grad_mode, form, emulate):
+    """configuration 1 (exp/log tape), any emulation policy: all results
+    bit-identical to the interpreter"""
     t = W.config_tape(1)
     boxes, splits = ragged_batch(t, 23, seed=5, max_split=40)
-    a, b = bound_both(t, boxes, splits, grad_mode=grad_mode, form=form)
+    a, b = bound_both(t, boxes, splits, grad_mode=grad_mode, form=form, emulate=emulate)
     for k in KEYS:
         assert same_bits(a[k], b[k]), k
 
@@ -127,14 +132,15 @@ def test_specialized_variable_and_constant_outputs(grad_mode):
         assert np.array_equal(b[k], ref[k]), k
 
 
-def test_specialized_full_size_config2_identical_to_interpreter():
+@pytest.mark.parametrize("emulate", [-1, 15])
+def test_specialized_full_size_config2_identical_to_interpreter(emulate):
     """configuration 2 at full size (16 nodes x 16^4 subdomains, autotuned,
     CUDA graph): bit-identical to the interpreter"""
     wl = W.config_workload(2)
     t = wl.tape
     boxes = W.bisection_frontier(t.root_box, 16, seed=20)
     splits = np.tile(wl.splits, (16, 1)).astype(np.int32)
-    a, b = bound_both(t, boxes, splits)
+    a, b = bound_both(t, boxes, splits, emulate=emulate)
     for k in KEYS:
         assert same_bits(a[k], b[k]), k
 

@@ -491,3 +491,117 @@ def test_generator_is_deterministic_and_sized():
         assert np.all(t1.a[interior] < idx[interior])
         assert np.all(t1.b[interior] < idx[interior])
     assert W.Xoshiro256ss(1).next_u64() == W.Xoshiro256ss(1).next_u64()
+
+
+# ------------------------------------------------ constraint propagation
+
+def _toy(n, build, box):
+    B = P.Builder(n)
+    build(B, [B.x(i) for i in range(n)])
+    return B.tape(box, "toy")
+
+
+def test_propagation_closed_forms():
+    """hand-derived tightenings: the unit disc, a linear cut, an equality,
+    an objective cut, an impossible constraint"""
+    def disc(B, x):
+        B.output(B.add(x[0], x[1]), P.KIND_OBJ)
+        B.output(B.sub(B.add(B.sqr(x[0]), B.sqr(x[1])), B.const(1.0)), P.KIND_INEQ)
+    t = _toy(2, disc, [[-2.0, 2.0], [-2.0, 2.0]])
+    bx, inf = oracle.propagate(t, t.root_box)
+    assert not inf[0] and np.array_equal(bx[0], [[-1.0, 1.0], [-1.0, 1.0]])
+
+    def cut(B, x):   # x0 + x1 + 3 <= 0 on [-2, 2]^2: both in [-2, -1]
+        B.output(B.mul(x[0], x[1]), P.KIND_OBJ)
+        B.output(B.add(B.add(x[0], x[1]), B.const(3.0)), P.KIND_INEQ)
+    t = _toy(2, cut, [[-2.0, 2.0], [-2.0, 2.0]])
+    bx, inf = oracle.propagate(t, t.root_box)
+    assert not inf[0] and np.array_equal(bx[0], [[-2.0, -1.0], [-2.0, -1.0]])
+
+    def eq(B, x):    # x0 - x1 = 0 on [0, 2] x [1, 3]: both in [1, 2]
+        B.output(B.add(x[0], x[1]), P.KIND_OBJ)
+        B.output(B.sub(x[0], x[1]), P.KIND_EQ)
+    t = _toy(2, eq, [[0.0, 2.0], [1.0, 3.0]])
+    bx, inf = oracle.propagate(t, t.root_box)
+    assert not inf[0] and np.array_equal(bx[0], [[1.0, 2.0], [1.0, 2.0]])
+
+    def obj(B, x):   # f = x0 (a variable entry), cut f <= 0.5
+        B.output(x[0], P.KIND_OBJ)
+    t = _toy(1, obj, [[-1.0, 1.0]])
+    bx, inf = oracle.propagate(t, t.root_box, ub=0.5)
+    assert not inf[0] and np.array_equal(bx[0], [[-1.0, 0.5]])
+    bx, inf = oracle.propagate(t, t.root_box, ub=-2.0)
+    assert inf[0]
+
+    def never(B, x):  # x0^2 + 1 <= 0 has no solution
+        B.output(x[0], P.KIND_OBJ)
+        B.output(B.add(B.sqr(x[0]), B.const(1.0)), P.KIND_INEQ)
+    t = _toy(1, never, [[-3.0, 3.0]])
+    assert oracle.propagate(t, t.root_box)[1][0]
+
+
+def test_propagation_through_exp_log_div_sqrt():
+    """exp(x0) <= 2 gives x0 <= log 2 (within the widening); log(x0) >= 1
+    gives x0 >= e; x0 / x1 <= 1 with x1 in [1, 2] gives x0 <= 2;
+    sqrt(x0) <= 3 gives x0 <= 9"""
+    def f(B, x):
+        B.output(B.add(x[0], x[1]), P.KIND_OBJ)
+        B.output(B.sub(B.exp(x[0]), B.const(2.0)), P.KIND_INEQ)
+    t = _toy(2, f, [[-3.0, 3.0], [-1.0, 1.0]])
+    bx, _ = oracle.propagate(t, t.root_box)
+    assert math.log(2.0) <= bx[0, 0, 1] <= math.log(2.0) * (1 + 8e-16) and bx[0, 0, 0] == -3.0
+
+    def g(B, x):
+        B.output(x[0], P.KIND_OBJ)
+        B.output(B.sub(B.const(1.0), B.log(x[0])), P.KIND_INEQ)
+    t = _toy(1, g, [[0.5, 10.0]])
+    bx, _ = oracle.propagate(t, t.root_box)
+    assert math.e * (1 - 8e-16) <= bx[0, 0, 0] <= math.e and bx[0, 0, 1] == 10.0
+
+    def h(B, x):
+        B.output(x[0], P.KIND_OBJ)
+        B.output(B.sub(B.div(x[0], x[1]), B.const(1.0)), P.KIND_INEQ)
+        B.output(B.sub(B.sqrt(B.add(x[0], B.const(5.0))), B.const(3.0)), P.KIND_INEQ)
+    t = _toy(2, h, [[-4.0, 10.0], [1.0, 2.0]])
+    bx, _ = oracle.propagate(t, t.root_box)
+    assert bx[0, 0, 1] == 2.0 and bx[0, 1].tolist() == [1.0, 2.0]
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_propagation_is_sound_on_sampled_points(seed):
+    """brute force: every sampled point that certainly satisfies the
+    constraints (and f <= ub) lies in the tightened box, boxes declared
+    infeasible hold no such point, and no box grows"""
+    t = W.random_problem(3, 60, 2, W.OPS_ALL, [[-3, 2]] * 3, 300 + seed, "sound")
+    rng = np.random.default_rng(seed)
+    boxes = W.bisection_frontier(t.root_box, 40, seed=seed)
+    pts = np.concatenate([rng.uniform(boxes[:, :, 0][:, None, :], boxes[:, :, 1][:, None, :], (40, 400, 3))])
+    vals = P.np_eval(t, pts.reshape(-1, 3)).reshape(40, 400, -1)
+    ineq = [q for q in range(t.n_out) if t.out_kind[q] == W.KIND_INEQ]
+    obj = [q for q in range(t.n_out) if t.out_kind[q] == W.KIND_OBJ][0]
+    ub = float(np.median(vals[:, :, obj]))
+    bx, inf = oracle.propagate(t, boxes, ub=ub)
+    assert np.all(bx[:, :, 0] >= boxes[:, :, 0]) and np.all(bx[:, :, 1] <= boxes[:, :, 1])
+    scale = 1e-9 * (1 + np.abs(vals))
+    good = np.all(vals[:, :, ineq] <= -scale[:, :, ineq], axis=2) & (vals[:, :, obj] <= ub - scale[:, :, obj])
+    assert good.sum() > 50   # the check has teeth
+    for k in range(40):
+        p = pts[k][good[k]]
+        if inf[k]:
+            assert len(p) == 0
+        else:
+            assert np.all(p >= bx[k, :, 0]) and np.all(p <= bx[k, :, 1])
+    assert inf.sum() + (bx != boxes).any(axis=(1, 2)).sum() > 0   # and propagation did something
+
+
+def test_bnb_with_propagation_brackets_closed_form_minima():
+    """the oracle B&B with propagation still brackets the known minima"""
+    T = P.shifted_squares(2, [0.3, -1.1], [[-2, 2]] * 2)
+    r = oracle.bnb(T, splits=[8, 8], eps_abs=1e-6, eps_rel=0.0, grad_mode="adjoint", max_nodes=20000, propagate=3)
+    assert r["converged"] and r["lb"] <= 0.0 <= r["ub"] and r["ub"] - r["lb"] <= 1e-6
+    t = P.constrained_toy("feasible")   # min x0 + x1 on the unit disc: -sqrt(2)
+    r = oracle.bnb(t, splits=[6, 6], eps_abs=1e-6, eps_rel=0.0, grad_mode="adjoint", max_nodes=50000, propagate=3)
+    assert r["converged"] and r["lb"] - 1e-12 <= -math.sqrt(2.0) <= r["ub"] + 1e-12
+    t = P.constrained_toy("infeasible")
+    r = oracle.bnb(t, splits=[6, 6], eps_abs=1e-6, eps_rel=0.0, propagate=3)
+    assert r["converged"] and r["lb"] == math.inf and r["nodes"] == 0

@@ -70,6 +70,15 @@ MUTANTS = [
     ("square of a straddling interval keeps a positive lower end",
      "    else { r.lo = 0.0; r.hi = max2(prod_up(x.lo, x.lo), prod_up(x.hi, x.hi)); }",
      "    else { r.lo = min2(prod_dn(x.lo, x.lo), prod_dn(x.hi, x.hi)); r.hi = max2(prod_up(x.lo, x.lo), prod_up(x.hi, x.hi)); }"),
+    ("propagation projects a difference onto its subtrahend with the wrong sign",
+     "case OP_SUB: ok = meet_iv(&V[a], iv_add(z, V[b])) && meet_iv(&V[b], iv_sub(V[a], z)); break;",
+     "case OP_SUB: ok = meet_iv(&V[a], iv_add(z, V[b])) && meet_iv(&V[b], iv_sub(z, V[a])); break;"),
+    ("propagation of a square keeps only the nonnegative root",
+     "else { r.lo = -r_hi; r.hi = r_hi; }",
+     "else { r.lo = r_lo; r.hi = r_hi; }"),
+    ("propagation cuts the objective at the wrong side",
+     "else if (ub < INFINITY) { iv f = {-INFINITY, ub}; ok = meet_iv(z, f); }",
+     "else if (ub < INFINITY) { iv f = {ub, INFINITY}; ok = meet_iv(z, f); }"),
     ("adaptive partitioning grows the narrowest dimension",
      "                double v = rw[i] / out[i];\n                if (v > bestv) { bestv = v; best = i; }",
      "                double v = 1.0 / (rw[i] / out[i] + 1e-300);\n                if (v > bestv) { bestv = v; best = i; }"),
