@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--bnb", type=int, default=1, help="run the B&B time-to-gap comparison (rank 0)")
     ap.add_argument("--bnb-time", type=float, default=45.0, help="time cap per B&B run, seconds")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target oracle sample time")
+    ap.add_argument("--bnb-configs", type=str, default="",
+                    help="comma list of configurations (2, 3, 5) for a B&B time-to-gap study with the host "
+                         "additions switched on one by one (minutes; off by default)")
+    ap.add_argument("--bnb-config-cap", type=float, default=90.0, help="time cap per run of that study, seconds")
     ap.add_argument("--specialize", type=int, default=1,
                     help="1: tape-specialised bounding kernel (NVRTC at problem creation); 0: tape interpreter")
     ap.add_argument("--patterns", type=int, default=1,
@@ -298,6 +302,8 @@ def main():
         line["interpreter"] = interpreter_compare(t, boxes_d, splits_d, out, flush, stream, subs_step, step_s)
     if rank == 0 and world == 1 and args.bnb:
         line["bnb"] = bnb_compare(t, wl, args.bnb_time)
+    if rank == 0 and world == 1 and args.bnb_configs:
+        line["bnb_configs"] = bnb_config_study([int(c) for c in args.bnb_configs.split(",")], args.bnb_config_cap)
     if rank == 0 and world == 1 and args.patterns:
         line["differentiation"] = differentiation_compare()
         line["batching"] = batching_compare()
@@ -453,6 +459,35 @@ def bnb_compare(t, wl, cap):
     if c["converged"] and b["converged"]:
         res["speedup_time_to_gap_with_host_additions"] = b["seconds"] / c["seconds"]
     return res
+
+
+def bnb_config_study(configs, cap):
+    """B&B to each configuration's gap: adjoint + batched (32 parents per
+    iteration), then + constraint propagation, + CPU/GPU overlap, + the
+    tape-specialised kernel (not for configuration 5, whose tapes are too
+    large to compile quickly). Configurations 3 and 5 split each node by the
+    adaptive picker (2^15 and 2^18 subdomains per node)."""
+    from paper_2507_20769_gb300 import ivb
+    from paper_2507_20769_gb300 import workloads as W
+    out = []
+    for cfg in configs:
+        wl = W.config_workload(cfg)
+        t = wl.tape
+        split = (dict(splits=wl.splits) if wl.splits is not None
+                 else dict(target=1 << (18 if cfg == 5 else 15), strategy="adaptive"))
+        arms = [("adjoint_batched", {}, {}), ("+propagate", {}, dict(propagate=3)),
+                ("+propagate+overlap", {}, dict(propagate=3, overlap=1))]
+        if cfg != 5:
+            arms.append(("+propagate+overlap+specialised", dict(specialize=1), dict(propagate=3, overlap=1)))
+        for name, popts, bopts in arms:
+            with ivb.Problem(t, grad_mode="adjoint", batched=1, **popts) as p:
+                r = p.bnb_solve(t.root_box, batch=32, eps_abs=wl.gap_abs, eps_rel=wl.gap_rel, time_limit=cap,
+                                **split, **bopts)
+            gap = r["ub"] - r["lb"]
+            out.append({"config": cfg, "arm": name, "seconds": r["seconds"], "converged": r["converged"],
+                        "nodes": r["nodes"], "lb": r["lb"], "ub": r["ub"],
+                        "rel_gap": gap / abs(r["ub"]) if np.isfinite(gap) and r["ub"] != 0 else None})
+    return out
 
 
 if __name__ == "__main__":
