@@ -349,8 +349,8 @@ def interpreter_compare(t, boxes_d, splits_d, out, flush, stream, subs_step, ste
 # source files each bounding kernel is built from (the traffic record is valid
 # only while they are unchanged)
 KERNEL_SOURCES = {
-    "interpreter": ("ivb_kernels.cu", "ivb_bound_common.cuh", "ivb_iv.cuh", "ivb_fp64x.cuh"),
-    "specialised": ("ivb_jit.cpp", "ivb_bound_common.cuh", "ivb_iv.cuh", "ivb_fp64x.cuh"),
+    "interpreter": ("ivb_kernels.cu", "ivb_bound_common.cuh", "ivb_iv.cuh", "ivb_fp64x.cuh", "ivb_emu.cuh"),
+    "specialised": ("ivb_jit.cpp", "ivb_bound_common.cuh", "ivb_iv.cuh", "ivb_fp64x.cuh", "ivb_emu.cuh"),
 }
 
 

@@ -129,8 +129,9 @@ __device__ __forceinline__ void decode_dim(const char* rec, int n, int i, unsign
     kk /= N;
     const double lo = __ldg(rlo + i), hi = __ldg(rlo + n + i), h = __ldg(rlo + 2 * n + i);
     double e0 = lo, e1 = hi;
-    if (j > 0) e0 = imin(imax(__dadd_rn(lo, __dmul_rn((double)j, h)), lo), hi);
-    if (j + 1 < N) e1 = imin(imax(__dadd_rn(lo, __dmul_rn((double)(j + 1), h)), lo), hi);
+    // j and j + 1 (< 2^31) converted exactly on the integer pipe
+    if (j > 0) e0 = imin(imax(__dadd_rn(lo, __dmul_rn(int_to_double((int)j), h)), lo), hi);
+    if (j + 1 < N) e1 = imin(imax(__dadd_rn(lo, __dmul_rn(int_to_double((int)(j + 1)), h)), lo), hi);
     X = mk(e0, e1);
     c = __dmul_rn(__dadd_rn(e0, e1), 0.5);
 }

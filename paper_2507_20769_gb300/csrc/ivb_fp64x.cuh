@@ -169,9 +169,16 @@ __device__ __forceinline__ double sqrt_dir(double x, bool up) {
 }
 
 // ---------------------------------------------------------------- exp
-// double whose value is the integer k (|k| < 2^31), one FP64 add
+// double whose value is the integer k (|k| < 2^31), assembled on the integer
+// pipe: sign, biased exponent 1023 + floor(log2 |k|) from the leading-zero
+// count, and |k| shifted under the hidden bit (exact)
 __device__ __forceinline__ double int_to_double(int k) {
-    return from_bits(0x4338000000000000LL + (long long)k) - 6755399441055744.0;
+    const unsigned a = k < 0 ? 0u - (unsigned)k : (unsigned)k;
+    const int msb = 31 - __clz((int)a);                       // a > 0: position of the leading one
+    const unsigned long long mant = ((unsigned long long)a << (52 - msb)) & 0x000FFFFFFFFFFFFFULL;
+    const unsigned long long b = ((unsigned long long)(k < 0) << 63) |
+                                 ((unsigned long long)(1023 + msb) << 52) | mant;
+    return from_bits(a != 0u ? (long long)b : 0LL);
 }
 
 // exp(x) for |x| <= 700 (fast path): one final rounding plus < 2^-58 relative
