@@ -309,7 +309,7 @@ std::string compile_tape(const ivb_tape* t, HostProgram& P, std::vector<Ins>& in
     for (int64_t* c : {P.cnt_fwd, P.cnt_adj}) {
         c[RN] += 6LL * n;                                   // decode: endpoints and centre
         count_values(P.pt_begin, P.pt_count, c);            // point sweep f(c)
-        c[ADD] += 4LL * n * no;                             // MVF: X - c and the sum
+        c[ADD] += 2LL * n + 2LL * n * no;                   // MVF: X - c once per dimension, the sum per output
         c[MUL] += 2LL * n * no;
     }
     count_tangents(P.tan_begin, P.tan_count, P.cnt_fwd);

@@ -89,14 +89,16 @@ __device__ __forceinline__ double rcp_seed(double y) {
 __device__ __forceinline__ bool safe_e(int E) { return E >= 64 && E <= 1980; }
 
 // ---------------------------------------------------------------- reciprocal
-// correctly rounded 1/y toward -inf (up = false) or +inf (up = true), y > 0
+// correctly rounded 1/y toward -inf (up = false) or +inf (up = true), y > 0.
+// With e = 1 - y r0 (|e| < 2^-21, computed with one rounding), 1/y =
+// r0 / (1 - e) = r0 (1 + e + e^2 + e^3 + ...): r0 + r0 (e + e^2) leaves e^3 <
+// 2^-63, so one rounding puts r within 0.5 ulp + 2^-62 relative of 1/y, and the
+// exact residual 1 - y r picks the directed neighbour.
 __device__ __forceinline__ double rcp_dir_pos(double y, bool up) {
     if (safe_e(bexp(y))) {
-        double r = rcp_seed(y);
-        double e = __fma_rn(-y, r, 1.0);
-        r = __fma_rn(r, e, r);
-        e = __fma_rn(-y, r, 1.0);
-        r = __fma_rn(r, e, r);                       // within 0.5 ulp + 2^-80 relative
+        const double r0 = rcp_seed(y);
+        const double e = __fma_rn(-y, r0, 1.0);
+        const double r = __fma_rn(r0, __fma_rn(e, e, e), r0);
         if (!mant_zero(r)) {
             const double rho = __fma_rn(-y, r, 1.0);  // sign(1/y - r)
             if (up) return (sgn_le0(rho)) ? r : up1(r);
@@ -154,11 +156,12 @@ __device__ __forceinline__ double sqrt_dir(double x, bool up) {
         const int h = (E - 1023 - odd) / 2;          // exact: E - 1023 - odd is even
         const double r0 = from_bits(((long long)(fe - 127 - h + 1023) << 52) | ((long long)(rb & 0x7FFFFF) << 29));
         double g = x * r0;                           // ~sqrt(x)
-        double hh = from_bits(bits(r0) - (1LL << 52));   // r0 / 2, exact
+        const double hh = from_bits(bits(r0) - (1LL << 52));   // r0 / 2, exact
         const double eps = __fma_rn(-g, hh, 0.5);
-        g = __fma_rn(g, eps, g);
-        hh = __fma_rn(hh, eps, hh);
-        g = __fma_rn(__fma_rn(-g, g, x), hh, g);     // within 0.5 ulp + tiny
+        g = __fma_rn(g, eps, g);                     // relative error < 1.5 (2^-21)^2 < 2^-41
+        // last step: the remainder x - g^2 is < 2^-40 x, so the seed-accurate 1/(2 sqrt x)
+        // (2^-21) leaves < 2^-62 relative: within 0.5 ulp + 2^-62 after one rounding
+        g = __fma_rn(__fma_rn(-g, g, x), hh, g);
         if (!mant_zero(g)) {
             const double d = __fma_rn(-g, g, x);     // sign(sqrt(x) - g)
             if (up) return sgn_le0(d) ? g : up1(g);
