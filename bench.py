@@ -255,17 +255,22 @@ def main():
     names = ("dfma", "dadd", "dmul", "ddiv", "drcp", "dsqrt", "exp", "log",
              "own_rcp", "own_div", "own_sqrt", "own_exp", "own_log", "emu_mul", "mixed_mul", "emu_add", "mixed_add")
     rates = {k: ivb.ivb_fp64_probe(k) for k in names}
-    peak = rates["dfma"]
+    probe = rates["dfma"]   # measured DFMA lane-op/s: the unit of the per-primitive costs
+    # peak of the FP64 pipe from unit counts and clocks: 2 DFMA lanes per clock per SM on
+    # GB300 (ncu's dfma peak_sustained), times the SMs and the SM clock sampled during the steps
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clock_mhz = clk.get("sm_mhz") or 2070.0
+    peak = 2.0 * sms * clock_mhz * 1e6
     for k, extra in (("log", "dadd"), ("own_log", "dadd"), ("dsqrt", "dmul"), ("own_sqrt", "dmul")):
         # these probes carry one extra round-to-nearest add / multiply per operation
         rates[k] = 1.0 / max(1.0 / rates[k] - 1.0 / rates[extra], 1e-30)
     # cost of each category in DFMA issue slots: the primitives the kernel runs
-    cost = {"addsub": peak / rates["dadd"], "mul": peak / rates["dmul"], "div": peak / rates["own_div"],
-            "rcp": peak / rates["own_rcp"], "sqrt": peak / rates["own_sqrt"], "exp": peak / rates["own_exp"],
-            "log": peak / rates["own_log"], "rn": peak / rates["dadd"]}
-    vendor = {"addsub": peak / rates["dadd"], "mul": peak / rates["dmul"], "div": peak / rates["ddiv"],
-              "rcp": peak / rates["drcp"], "sqrt": peak / rates["dsqrt"], "exp": peak / rates["exp"],
-              "log": peak / rates["log"], "rn": peak / rates["dadd"]}
+    cost = {"addsub": probe / rates["dadd"], "mul": probe / rates["dmul"], "div": probe / rates["own_div"],
+            "rcp": probe / rates["own_rcp"], "sqrt": probe / rates["own_sqrt"], "exp": probe / rates["own_exp"],
+            "log": probe / rates["own_log"], "rn": probe / rates["dadd"]}
+    vendor = {"addsub": probe / rates["dadd"], "mul": probe / rates["dmul"], "div": probe / rates["ddiv"],
+              "rcp": probe / rates["drcp"], "sqrt": probe / rates["dsqrt"], "exp": probe / rates["exp"],
+              "log": probe / rates["log"], "rn": probe / rates["dadd"]}
     counts = p.op_counts()
     slots_per_sub = sum(counts[k] * cost[k] for k in counts)
     vendor_slots = sum(counts[k] * vendor[k] for k in counts)
@@ -275,8 +280,11 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
                 "unit": "G FP64 DFMA-slot/s", "frac": achieved / peak,
                 "traffic": traffic_for(subs_step, "specialised" if args.specialize else "interpreter"),
-                "peak_source": "measured live: DFMA lane-op/s of this GPU (ivb_fp64_probe), "
-                               f"= {2 * peak / 1e12:.3f} FP64 TFLOP/s",
+                "peak_source": f"derived: {sms} SMs x 2 FP64 lanes/clock x {clock_mhz:.0f} MHz (SM clock sampled "
+                               f"during the steps) = {2 * peak / 1e12:.3f} FP64 TFLOP/s",
+                "measured_probe_peak": probe / 1e9, "frac_of_measured_probe": achieved / probe,
+                "probe_note": "ivb_fp64_probe: 8 independent DFMA chains per thread, 32 warps per SM; "
+                              "primitive costs are in units of this rate",
                 "work_per_subdomain": {"endpoint_ops": ops_per_sub, "dfma_slots": slots_per_sub,
                                        "counts": counts,
                                        "dfma_slots_with_cuda_intrinsics": vendor_slots},
