@@ -101,7 +101,8 @@ typedef struct {
                                   and tile on first use                       */
     int32_t block_threads;     /* threads per block; 0 = tuned / default     */
     int32_t blocks_per_sm;     /* resident blocks per SM; 0 = tuned/default  */
-    int32_t tile;              /* subdomains a block grabs at a time; 0 = auto */
+    int32_t tile;              /* subdomains a block grabs at a time; 0: as
+                                  many as it has threads (smallest tail)   */
     int32_t max_nodes;         /* capacity of one call (default 4096)       */
     int32_t frame_in_shared;   /* -1 auto (default), 0 global, 1 shared     */
     int32_t specialize;        /* 1: at creation, write the tape's programs

@@ -249,7 +249,7 @@ ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
         const int grid = p->sm_count * c.bps;
         if (!use_jit(p)) st = ensure_frame(p, grid, c.block);
         if (st) break;
-        const int tile = c.block * 4;
+        const int tile = c.block;   // one pass per grab: the smallest tail at the end of a launch
         for (int rep = 0; rep < 2 && !st; ++rep) {      // warm-up, then timed
             if (rep == 1) { cudaError_t ce = cudaEventRecord(e0, s); if (ce) { st = cuda_fail(p, ce, "event"); break; } }
             st = enqueue_bound(p, grid, c.block, tile, c.smem, p->max_nodes, s);
@@ -271,7 +271,7 @@ ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
     p->block = bc.block;
     p->bps = bc.bps;
     p->frame_smem = bc.smem;
-    p->tile = bc.block * 4;
+    p->tile = bc.block;
     p->tuned = true;
     p->cfg_ready = true;
     if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
@@ -289,7 +289,7 @@ ivb_status default_tuning(ivb_problem* p) {
     const int occ = reduce_occupancy(p, p->block, p->frame_smem);
     if (occ < 1) return fail(p, IVB_ENOTSUP, "launch configuration does not fit on an SM");
     if (p->bps > occ) p->bps = occ;
-    p->tile = p->opt.tile > 0 ? ((p->opt.tile + p->block - 1) / p->block) * p->block : p->block * 4;
+    p->tile = p->opt.tile > 0 ? ((p->opt.tile + p->block - 1) / p->block) * p->block : p->block;
     p->cfg_ready = true;
     const bool explicit_cfg = p->opt.block_threads > 0 || p->opt.blocks_per_sm > 0;
     if (!p->opt.autotune || explicit_cfg) p->tuned = true;
