@@ -106,15 +106,19 @@ typedef struct {
     int32_t max_nodes;         /* capacity of one call (default 4096)       */
     int32_t frame_in_shared;   /* -1 auto (default), 0 global, 1 shared     */
     int32_t specialize;        /* 1: at creation, write the tape's programs
-                                  out as a straight-line CUDA kernel, compile
-                                  it with NVRTC for sm_103a and use it for
+                                  out as straight-line CUDA, compile it with
+                                  NVRTC for sm_103a and use it for
                                   ivb_bound_nodes / _ex (bit-identical bounds,
                                   values in registers instead of frame memory;
                                   creation fails with IVB_ENOTSUP if it cannot
-                                  be compiled); 0 (default): tape interpreter;
-                                  -1: specialise when the tape is small enough
-                                  for a short compile (at most 4096 interval
-                                  operations per subdomain), else interpret  */
+                                  be compiled); the point sweep and each
+                                  output's sweeps are functions of their own
+                                  and the long primitives are called out of
+                                  line, which halves the compile time at the
+                                  same speed; 2: the same fully inlined;
+                                  0 (default): tape interpreter; -1: as 1 when
+                                  the tape has at most 1024 interval
+                                  operations per subdomain, else interpret  */
     int32_t emulate;           /* tape-specialised kernel only: endpoint
                                   operations computed by an exact emulation
                                   on the integer pipes (bit-identical to the
@@ -295,11 +299,13 @@ ivb_status ivb_get_specialization(ivb_problem* p, int32_t* active, int32_t* regi
                                   int32_t* local_bytes, double* compile_seconds, int32_t* emulate);
 
 /* Generate and compile (NVRTC, sm_103a) the tape-specialised kernel of a
- * tape without loading it -- needs no GPU. Reports ptxas' registers per
+ * tape without loading it -- needs no GPU; compact = 1 as for specialize = 1,
+ * 0 as for specialize = 2.
+ * Reports ptxas' registers per
  * thread and spill-store bytes, and the compile time (each may be NULL).
  * IVB_ETAPE for an invalid tape, IVB_ENOTSUP (message in ivb_last_error(NULL))
  * when the program does not compile. */
-ivb_status ivb_specialize_compile(const ivb_tape* tape, int32_t grad_mode, int32_t* registers,
+ivb_status ivb_specialize_compile(const ivb_tape* tape, int32_t grad_mode, int32_t compact, int32_t* registers,
                                   int32_t* spill_bytes, double* compile_seconds);
 
 /* Static count of the outward-rounded endpoint operations one subdomain

@@ -324,7 +324,8 @@ ivb_status deliver(ivb_problem* p, int n_nodes, double* out_lb, uint8_t* out_inf
 cudaError_t specialize(ivb_problem* p, const std::vector<Ins>& ins, const std::vector<RIns>& rins,
                        const std::vector<double>& consts, int mode, std::string* msg) {
     const int emu = p->opt.emulate >= 0 ? p->opt.emulate : kJitDefaultEmulate;
-    const std::string src = jit_source(p->P, ins, rins, consts, mode, kJitBlockMax, kJitMinBlocks, emu);
+    const bool compact = p->opt.specialize != 2;
+    const std::string src = jit_source(p->P, ins, rins, consts, mode, kJitBlockMax, kJitMinBlocks, emu, compact);
     std::vector<char> cubin;
     std::string tables;
     double secs = 0.0;
@@ -334,6 +335,7 @@ cudaError_t specialize(ivb_problem* p, const std::vector<Ins>& ins, const std::v
     if (ce != cudaSuccess) return ce;
     p->jit.mode = mode;
     p->jit.emulate = emu;
+    p->jit.compact = compact;
     p->jit.block_max = kJitBlockMax;
     p->jit.compile_seconds = secs;
     return cudaSuccess;
@@ -370,7 +372,7 @@ extern "C" ivb_status ivb_create_problem(const ivb_tape* tape, const ivb_options
     if (o.max_nodes < 1 || o.max_nodes > (1 << 20)) return fail(nullptr, IVB_EINVAL, "max_nodes must be in [1, 2^20]");
     if (o.block_threads < 0 || o.block_threads > 512 || (o.block_threads % 32))
         return fail(nullptr, IVB_EINVAL, "block_threads must be a multiple of 32 up to 512 (0 = auto)");
-    if (o.specialize < -1 || o.specialize > 1) return fail(nullptr, IVB_EINVAL, "specialize must be -1, 0 or 1");
+    if (o.specialize < -1 || o.specialize > 2) return fail(nullptr, IVB_EINVAL, "specialize must be -1, 0, 1 or 2");
     if (o.emulate < -1 || o.emulate > 15) return fail(nullptr, IVB_EINVAL, "emulate must be -1 or a bitmask in [0, 15]");
     if (o.specialize && o.block_threads > kJitBlockMax)
         return fail(nullptr, IVB_EINVAL, "block_threads above 256 with a tape-specialised kernel");
@@ -456,13 +458,13 @@ extern "C" ivb_status ivb_create_problem(const ivb_tape* tape, const ivb_options
         const int64_t* cnt = o.grad_mode == IVB_GRAD_ADJOINT ? p->P.cnt_adj : p->P.cnt_fwd;
         long long ops = 0;
         for (int k = 0; k < IVB_CNT_N; ++k) ops += cnt[k];
-        if (o.specialize == 1 || ops / 2 <= kJitAutoMaxOps) {
+        if (o.specialize >= 1 || ops / 2 <= kJitAutoMaxOps) {
             const int mode = o.grad_mode == IVB_GRAD_ADJOINT ? KM_ADJ_REDUCE : KM_FWD_REDUCE;
             std::string msg;
             const cudaError_t ce = specialize(p, ins, rins, consts, mode, &msg);
             if (ce != cudaSuccess || !msg.empty()) {
                 jit_unload(p->jit);
-                if (o.specialize == 1) {
+                if (o.specialize >= 1) {
                     ivb_destroy(p);
                     if (ce != cudaSuccess)
                         return fail(nullptr, ce == cudaErrorMemoryAllocation ? IVB_ENOMEM : IVB_ECUDA,
@@ -759,8 +761,8 @@ extern "C" ivb_status ivb_get_specialization(ivb_problem* p, int32_t* active, in
     return IVB_OK;
 }
 
-extern "C" ivb_status ivb_specialize_compile(const ivb_tape* tape, int32_t grad_mode, int32_t* registers,
-                                             int32_t* spill_bytes, double* seconds) {
+extern "C" ivb_status ivb_specialize_compile(const ivb_tape* tape, int32_t grad_mode, int32_t compact,
+                                             int32_t* registers, int32_t* spill_bytes, double* seconds) {
     std::string e = validate_tape(tape);
     if (!e.empty()) return fail(nullptr, IVB_ETAPE, e);
     if (grad_mode != IVB_GRAD_FORWARD && grad_mode != IVB_GRAD_ADJOINT)
@@ -772,7 +774,8 @@ extern "C" ivb_status ivb_specialize_compile(const ivb_tape* tape, int32_t grad_
     e = compile_tape(tape, P, ins, rins, consts);
     if (!e.empty()) return fail(nullptr, IVB_ENOTSUP, e);
     const int mode = grad_mode == IVB_GRAD_ADJOINT ? KM_ADJ_REDUCE : KM_FWD_REDUCE;
-    const std::string src = jit_source(P, ins, rins, consts, mode, kJitBlockMax, kJitMinBlocks, kJitDefaultEmulate);
+    const std::string src =
+        jit_source(P, ins, rins, consts, mode, kJitBlockMax, kJitMinBlocks, kJitDefaultEmulate, compact != 0);
     std::vector<char> cubin;
     std::string tables;
     int regs = 0, spill = 0;

@@ -90,6 +90,13 @@ __device__ __forceinline__ double next_dn(double y) { return ineg(next_up(ineg(y
 #define IVB_EMU 0
 #endif
 
+// Inlining of the long primitives (reciprocal, division, square root, exp,
+// log). Inline by default; a tape-specialised kernel compiled in compact mode
+// calls them out of line, which keeps its code and its compile time small.
+#ifndef IVB_HEAVY
+#define IVB_HEAVY __forceinline__
+#endif
+
 namespace ivb {
 
 // ---------------------------------------------------------------- endpoints
@@ -203,14 +210,14 @@ template <int E> __device__ __forceinline__ iv iv_sqr_t(iv x) {
 __device__ __forceinline__ iv iv_sqr(iv x) { return iv_sqr_t<IVB_EMU>(x); }
 
 // reciprocal of an interval without 0 (ENTIRE otherwise)
-__device__ __forceinline__ iv iv_recip(iv y) {
+__device__ IVB_HEAVY iv iv_recip(iv y) {
     if (!(gt0(y.lo) || lt0(y.hi))) return entire();
     return mk(rcp_dn(y.hi), rcp_up(y.lo));
 }
 __device__ __forceinline__ iv iv_recip_pos(iv y) { return gt0(y.lo) ? iv_recip(y) : entire(); }
 
 // quotient for 0 not in y and finite endpoints (ENTIRE otherwise)
-__device__ __forceinline__ iv iv_div(iv x, iv y) {
+__device__ IVB_HEAVY iv iv_div(iv x, iv y) {
     const bool ypos = gt0(y.lo), yneg = lt0(y.hi);
     if (!(ypos || yneg) || has_inf(x) || has_inf(y)) return entire();
     // for y < 0 use x/y = (-x)/(-y) with -y > 0 (negations are exact)
@@ -223,7 +230,7 @@ __device__ __forceinline__ iv iv_div(iv x, iv y) {
     return mk(div_dir_pos(xl, dl, rl, false), div_dir_pos(xh, dh, rh, true));
 }
 
-__device__ __forceinline__ iv iv_sqrt(iv x) {
+__device__ IVB_HEAVY iv iv_sqrt(iv x) {
     if (lt0(x.lo)) return entire();
     return mk(sqrt_dir(x.lo, false), sqrt_dir(x.hi, true));
 }
@@ -238,8 +245,8 @@ __device__ __forceinline__ double exp_up(double x) { return exp_dir(x, true); }
 __device__ __forceinline__ double log_dn(double x) { return log_dir(x, false); }
 __device__ __forceinline__ double log_up(double x) { return log_dir(x, true); }
 
-__device__ __forceinline__ iv iv_exp(iv x) { return mk(exp_dn(x.lo), exp_up(x.hi)); }
-__device__ __forceinline__ iv iv_log(iv x) {
+__device__ IVB_HEAVY iv iv_exp(iv x) { return mk(exp_dn(x.lo), exp_up(x.hi)); }
+__device__ IVB_HEAVY iv iv_log(iv x) {
     if (!gt0(x.lo)) return entire();
     return mk(log_dn(x.lo), log_up(x.hi));
 }

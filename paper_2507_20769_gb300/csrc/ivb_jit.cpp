@@ -252,14 +252,45 @@ struct Gen {
         line(ind, "}");
     }
 
-    std::string kernel(int mode, int block_max, int min_blocks, int emulate) {
+    std::string kernel(int mode, int block_max, int min_blocks, int emulate, bool compact) {
         out.clear();
         line(0, "#define IVB_EMU " + S(emulate));
+        if (compact) line(0, "#define IVB_HEAVY __noinline__");
         line(0, "typedef signed char int8_t; typedef unsigned char uint8_t;");
         line(0, "typedef short int16_t; typedef unsigned short uint16_t;");
         line(0, "typedef int int32_t; typedef unsigned int uint32_t;");
         line(0, "typedef long long int64_t; typedef unsigned long long uint64_t;");
         line(0, "#include \"ivb_bound_common.cuh\"");
+        // compact adjoint mode: the point sweep and each output's sweeps in functions of their own
+        const bool split = compact && mode == KM_ADJ_REDUCE;
+        if (split) {
+            line(0, "namespace ivb {");
+            line(0, "__device__ __noinline__ void jit_point(const double* __restrict__ cv, iv* __restrict__ fc) {");
+            for (int i = 0; i < n; ++i) line(1, "const double c" + S(i) + " = cv[" + S(i) + "];");
+            decls(1, "p", P.pt_slots);
+            values(1, 'p', P.pt_begin, P.pt_count);
+            for (int o = 0; o < no; ++o)
+                line(1, "fc[" + S(o) + "] = " + val('p', (uint32_t)P.pt_out_kind[o], (uint32_t)P.pt_out_ref[o]) + ";");
+            line(0, "}");
+            for (int o = 0; o < no; ++o) {
+                const AdjProgram& A = P.adj[o];
+                line(0, "__device__ __noinline__ iv jit_out" + S(o) +
+                            "(const iv* __restrict__ Xv, const double* __restrict__ cv, iv fc, int form) {");
+                for (int i = 0; i < n; ++i)
+                    line(1, "const iv X" + S(i) + " = Xv[" + S(i) + "]; const double c" + S(i) + " = cv[" + S(i) + "];");
+                decls(1, "r", A.tape_records);
+                decls(1, "w", A.adj_slots);
+                decls(1, "g", n);
+                values(1, 'r', A.fw_begin, A.fw_count);
+                if (A.out_wslot >= 0) line(1, "w" + S(A.out_wslot) + " = one();");
+                reverse(1, A);
+                line(1, "iv mvf = fc;");
+                for (int i = 0; i < n; ++i) line(1, "mvf = mvf_term(mvf, g" + S(i) + ", X" + S(i) + ", c" + S(i) + ");");
+                line(1, "return final_form(form, mvf, " + val('r', (uint32_t)A.out_kind_ref, (uint32_t)A.out_ref) + ");");
+                line(0, "}");
+            }
+            line(0, "}  // namespace ivb");
+        }
         line(0, "extern \"C\" __global__ void __launch_bounds__(" + S(block_max) + ", " + S(min_blocks) +
                     ") ivb_jit_bound(const ivb::KParams P) {");
         line(1, "using namespace ivb;");
@@ -282,14 +313,31 @@ struct Gen {
         for (int i = 0; i < n; ++i) line(d, "decode_dim(s.rec, " + S(n) + ", " + S(i) + ", kk, X" + S(i) + ", c" + S(i) + ");");
         // Step 2a: point sweep
         decls(d, "fc", no);
+        if (split) {
+            std::string xs = "const iv Xv[" + S(n) + "] = {", cs = "const double cv[" + S(n) + "] = {";
+            for (int i = 0; i < n; ++i) { xs += (i ? ", X" : "X") + S(i); cs += (i ? ", c" : "c") + S(i); }
+            line(d, xs + "};");
+            line(d, cs + "};");
+            line(d, "iv fcv[" + S(no) + "];");
+            line(d, "jit_point(cv, fcv);");
+            for (int o = 0; o < no; ++o) line(d, "fc" + S(o) + " = fcv[" + S(o) + "];");
+            // Step 2b: one call per output; the tests of finish() on its result
+            for (int o = 0; o < no; ++o) {
+                line(d, "F" + S(o) + " = jit_out" + S(o) + "(Xv, cv, fc" + S(o) + ", P.form);");
+                line(d, "if (excludes_feasible(" + S(P.out_kind[o]) + "u, F" + S(o) + ")) cert = true;");
+                if (o == P.obj) line(d, "obj_lo = F" + S(o) + ".lo;");
+            }
+        } else {
         line(d, "{");
         decls(d + 1, "p", P.pt_slots);
         values(d + 1, 'p', P.pt_begin, P.pt_count);
         for (int o = 0; o < no; ++o)
             line(d + 1, "fc" + S(o) + " = " + val('p', (uint32_t)P.pt_out_kind[o], (uint32_t)P.pt_out_ref[o]) + ";");
         line(d, "}");
+        }
         // Step 2b
-        if (mode == KM_FWD_REDUCE) {
+        if (split) {
+        } else if (mode == KM_FWD_REDUCE) {
             line(d, "{");
             const int e = d + 1;
             for (int k = 0; k < P.tan_slots; ++k) {
@@ -341,9 +389,10 @@ struct Gen {
 }  // namespace
 
 std::string jit_source(const HostProgram& P, const std::vector<Ins>& ins, const std::vector<RIns>& rins,
-                       const std::vector<double>& consts, int mode, int block_max, int min_blocks, int emulate) {
+                       const std::vector<double>& consts, int mode, int block_max, int min_blocks, int emulate,
+                       bool compact) {
     Gen g{P, ins.data(), rins.data(), consts.data(), P.n_vars, P.n_out, {}};
-    return g.kernel(mode, block_max, min_blocks, emulate);
+    return g.kernel(mode, block_max, min_blocks, emulate, compact);
 }
 
 std::string jit_compile(const std::string& src, std::vector<char>& cubin, std::string& tables_name, double* seconds,

@@ -13,8 +13,10 @@ namespace ivb {
 
 // generated kernels: __launch_bounds__(kJitBlockMax, kJitMinBlocks), i.e. at
 // most 128 registers per thread; specialize = -1 compiles tapes of at most
-// kJitAutoMaxOps interval operations per subdomain
-constexpr int kJitBlockMax = 256, kJitMinBlocks = 2, kJitAutoMaxOps = 4096;
+// kJitAutoMaxOps interval operations per subdomain (beyond that, compile time
+// grows to tens of seconds and the interpreter was within 5 % on the
+// configurations measured)
+constexpr int kJitBlockMax = 256, kJitMinBlocks = 2, kJitAutoMaxOps = 1024;
 // endpoint operations emulated on the integer pipes by default (ivb_iv.cuh
 // policy bits): none -- on configuration 2 no policy beat the FP64 pipe alone
 // by more than the noise (the kernel runs at its 128-register cap with 16
@@ -28,13 +30,15 @@ struct JitKernel {
     int mode = -1;             // KM_FWD_REDUCE or KM_ADJ_REDUCE
     int block_max = 0;         // __launch_bounds__ of the generated kernel
     int emulate = 0;           // emulation policy compiled in
+    bool compact = false;      // long primitives called out of line
     int regs = 0, local_bytes = 0, max_threads = 0;
     double compile_seconds = 0.0;
 };
 
 // CUDA C++ of the reduce-mode bounding kernel for this program
 std::string jit_source(const HostProgram& P, const std::vector<Ins>& ins, const std::vector<RIns>& rins,
-                       const std::vector<double>& consts, int mode, int block_max, int min_blocks, int emulate);
+                       const std::vector<double>& consts, int mode, int block_max, int min_blocks, int emulate,
+                       bool compact);
 // NVRTC for sm_103a; "" on success, else the compiler's message. With
 // `registers` / `spill_bytes` non-NULL, ptxas reports them (parsed from its log).
 std::string jit_compile(const std::string& src, std::vector<char>& cubin, std::string& tables_name, double* seconds,

@@ -95,7 +95,7 @@ def lib() -> ctypes.CDLL:
         L.ivb_bnb_solve.argtypes = [P, I32, P, P, P, P]
         L.ivb_get_specialization.argtypes = [P, P, P, P, P, P]
         L.ivb_propagate.argtypes = [P, I32, P, D, I32, P, P]
-        L.ivb_specialize_compile.argtypes = [P, I32, P, P, P]
+        L.ivb_specialize_compile.argtypes = [P, I32, I32, P, P, P]
         for f in ("ivb_create_problem", "ivb_bound_nodes", "ivb_bound_nodes_ex", "ivb_enclose", "ivb_point_grad",
                   "ivb_pick_splits", "ivb_get_tuning", "ivb_bnb_solve", "ivb_op_counts", "ivb_fp64_probe",
                   "ivb_bound_nodes_noalloc", "ivb_eval_op", "ivb_get_specialization", "ivb_specialize_compile",
@@ -214,7 +214,7 @@ def ivb_eval_op(opcode: int, x, y=None):
     return r
 
 
-def ivb_specialize_compile(tape, grad_mode="adjoint") -> dict:
+def ivb_specialize_compile(tape, grad_mode="adjoint", compact=True) -> dict:
     """generate and compile (NVRTC, no GPU needed) the tape-specialised
     kernel of a tape: ptxas registers, spill-store bytes, compile seconds"""
     recs = tape.records()
@@ -224,8 +224,8 @@ def ivb_specialize_compile(tape, grad_mode="adjoint") -> dict:
                  ok.ctypes.data)
     regs, spill, secs = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
     g = GRAD[grad_mode] if isinstance(grad_mode, str) else int(grad_mode)
-    _check(lib().ivb_specialize_compile(ctypes.byref(t), g, ctypes.byref(regs), ctypes.byref(spill),
-                                        ctypes.byref(secs)))
+    _check(lib().ivb_specialize_compile(ctypes.byref(t), g, int(bool(compact)), ctypes.byref(regs),
+                                        ctypes.byref(spill), ctypes.byref(secs)))
     return {"registers": regs.value, "spill_bytes": spill.value, "seconds": secs.value}
 
 

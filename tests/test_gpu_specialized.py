@@ -46,10 +46,12 @@ def same_bits(a, b):
     return a.shape == b.shape and np.array_equal(a.view(np.uint8), b.view(np.uint8))
 
 
-def bound_both(t, boxes, splits, **opts):
-    """results of the interpreter and of the specialised kernel, same options"""
+def bound_both(t, boxes, splits, spec_mode=1, **opts):
+    """results of the interpreter and of the specialised kernel (spec_mode 1:
+    per-output sweeps and long primitives out of line, or 2: fully inlined),
+    same options"""
     out = []
-    for spec in (0, 1):
+    for spec in (0, spec_mode):
         with ivb.Problem(t, specialize=spec, **opts) as p:
             if spec:
                 assert p.get_specialization()["active"]
@@ -59,16 +61,16 @@ def bound_both(t, boxes, splits, **opts):
 
 @pytest.mark.parametrize("grad_mode", ["forward", "adjoint"])
 @pytest.mark.parametrize("path", ["graph", "nograph", "plain"])
-@pytest.mark.parametrize("emulate", [0, 15])
-def test_specialized_bit_exact_rational_vs_oracle(grad_mode, path, emulate):
+@pytest.mark.parametrize("emulate,spec_mode", [(0, 1), (15, 1), (0, 2)])
+def test_specialized_bit_exact_rational_vs_oracle(grad_mode, path, emulate, spec_mode):
     """ragged batch (S from 1 to 216 per node, tiles crossing nodes), every
     launch path, endpoint operations on the FP64 pipe (0) or all emulated on
     the integer pipes (15): lb, infeasibility, centre upper bound and each
     output's hull equal the oracle's bit for bit"""
     t = rational_problem()
     boxes, splits = ragged_batch(t, 37, seed=11)
-    opts = dict(grad_mode=grad_mode, use_graph=int(path == "graph"), batched=int(path != "plain"), specialize=1,
-                emulate=emulate)
+    opts = dict(grad_mode=grad_mode, use_graph=int(path == "graph"), batched=int(path != "plain"),
+                specialize=spec_mode, emulate=emulate)
     with ivb.Problem(t, **opts) as p:
         assert p.get_specialization()["active"]
         r = p.bound_nodes_ex(boxes, splits, want_hull=True)
@@ -84,11 +86,12 @@ def test_specialized_bit_exact_rational_vs_oracle(grad_mode, path, emulate):
 @pytest.mark.parametrize("form", ["mvf", "nie", "mvf_nie"])
 @pytest.mark.parametrize("emulate", [-1, 0, 5, 10, 15])
 def test_specialized_identical_to_interpreter_exp_log(grad_mode, form, emulate):
-    """configuration 1 (exp/log tape), any emulation policy: all results
-    bit-identical to the interpreter"""
+    """configuration 1 (exp/log tape), any emulation policy, compact or not:
+    all results bit-identical to the interpreter"""
     t = W.config_tape(1)
     boxes, splits = ragged_batch(t, 23, seed=5, max_split=40)
-    a, b = bound_both(t, boxes, splits, grad_mode=grad_mode, form=form, emulate=emulate)
+    a, b = bound_both(t, boxes, splits, spec_mode=1 + (emulate == 5), grad_mode=grad_mode, form=form,
+                      emulate=emulate)
     for k in KEYS:
         assert same_bits(a[k], b[k]), k
 
@@ -121,10 +124,11 @@ def variable_and_constant_outputs():
 
 
 @pytest.mark.parametrize("grad_mode", ["forward", "adjoint"])
-def test_specialized_variable_and_constant_outputs(grad_mode):
+@pytest.mark.parametrize("spec_mode", [1, 2])
+def test_specialized_variable_and_constant_outputs(grad_mode, spec_mode):
     t = variable_and_constant_outputs()
     boxes, splits = ragged_batch(t, 11, seed=4)
-    a, b = bound_both(t, boxes, splits, grad_mode=grad_mode)
+    a, b = bound_both(t, boxes, splits, spec_mode=spec_mode, grad_mode=grad_mode)
     for k in KEYS:
         assert same_bits(a[k], b[k]), k
     ref = oracle.bound_nodes(t, boxes, splits, grad_mode=grad_mode, tight=True)
@@ -132,15 +136,15 @@ def test_specialized_variable_and_constant_outputs(grad_mode):
         assert np.array_equal(b[k], ref[k]), k
 
 
-@pytest.mark.parametrize("emulate", [-1, 15])
-def test_specialized_full_size_config2_identical_to_interpreter(emulate):
+@pytest.mark.parametrize("emulate,spec_mode", [(-1, 1), (15, 1), (-1, 2)])
+def test_specialized_full_size_config2_identical_to_interpreter(emulate, spec_mode):
     """configuration 2 at full size (16 nodes x 16^4 subdomains, autotuned,
     CUDA graph): bit-identical to the interpreter"""
     wl = W.config_workload(2)
     t = wl.tape
     boxes = W.bisection_frontier(t.root_box, 16, seed=20)
     splits = np.tile(wl.splits, (16, 1)).astype(np.int32)
-    a, b = bound_both(t, boxes, splits, emulate=emulate)
+    a, b = bound_both(t, boxes, splits, spec_mode=spec_mode, emulate=emulate)
     for k in KEYS:
         assert same_bits(a[k], b[k]), k
 

@@ -35,9 +35,10 @@ def every_op_tape():
 
 @pytest.mark.parametrize("grad_mode", ["adjoint", "forward"])
 @pytest.mark.parametrize("which", ["every_op", "config1"])
-def test_specialized_kernel_compiles(ivb, which, grad_mode):
+@pytest.mark.parametrize("compact", [False, True])
+def test_specialized_kernel_compiles(ivb, which, grad_mode, compact):
     t = every_op_tape() if which == "every_op" else W.config_tape(1)
-    r = ivb.ivb_specialize_compile(t, grad_mode)
+    r = ivb.ivb_specialize_compile(t, grad_mode, compact)
     assert 0 < r["registers"] <= 128
     assert r["spill_bytes"] >= 0 and r["seconds"] > 0
 
