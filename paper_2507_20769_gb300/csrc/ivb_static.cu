@@ -160,7 +160,7 @@ extern "C" ivb_status ivb_bound_nodes_noalloc(ivb_problem* p, int32_t n_nodes, c
     K.queue = queue;
     K.rec_bytes = rec;
     K.counter = counter;
-    K.tile = block * 4;
+    K.tile = block;   // one subdomain per thread per grab (the smallest tail)
     K.gframe = nullptr;
     K.frame_in_smem = 1;
     K.frame_units = fu;
