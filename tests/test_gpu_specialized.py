@@ -161,3 +161,62 @@ def test_specialize_auto_info_and_empty_batch():
         assert not p.get_specialization()["active"]
     with ivb.Problem(W.config_tape(1)) as p:
         assert not p.get_specialization()["active"]
+
+
+def shared_dag(n, n_ops, n_ineq, n_eq, ops, seed):
+    """random DAG whose outputs share subexpressions: every operand is any
+    earlier entry, so the outputs' cones overlap; some outputs are plain
+    variable or constant entries"""
+    rng = np.random.default_rng(seed)
+    Bd = P.Builder(n)
+    ids = list(range(n))
+    for _ in range(max(2, n // 4)):
+        ids.append(Bd.const(float(rng.uniform(-2, 2))))
+    names = {W.OP_ADD: Bd.add, W.OP_SUB: Bd.sub, W.OP_MUL: Bd.mul, W.OP_DIV: Bd.div, W.OP_SQR: Bd.sqr,
+             W.OP_SQRT: Bd.sqrt, W.OP_EXP: Bd.exp, W.OP_LOG: Bd.log, W.OP_NEG: Bd.neg}
+    for _ in range(n_ops):
+        op = int(rng.choice(ops))
+        a = ids[int(rng.integers(len(ids)))]
+        b = ids[int(rng.integers(len(ids)))]
+        if op in (W.OP_DIV,):      # keep divisors away from 0: b^2 + 1
+            b = Bd.add(Bd.sqr(b), Bd.const(1.0))
+        if op in (W.OP_SQRT, W.OP_LOG):
+            a = Bd.add(Bd.sqr(a), Bd.const(0.5))
+        if op == W.OP_EXP:
+            a = Bd.mul(Bd.const(0.01), a)
+        ids.append(names[op](a, b) if op in (W.OP_ADD, W.OP_SUB, W.OP_MUL, W.OP_DIV) else names[op](a))
+    interior = ids[n:]
+    Bd.output(interior[-1], P.KIND_OBJ)
+    for q in range(n_ineq):
+        pick = interior[int(rng.integers(len(interior)))]
+        Bd.output(Bd.sub(pick, Bd.const(float(rng.uniform(0, 3)))), P.KIND_INEQ)
+    for q in range(n_eq):
+        Bd.output(Bd.sub(ids[q % n], ids[(q + 1) % n]), P.KIND_EQ)
+    Bd.output(0, P.KIND_INEQ)                   # a variable entry as an output
+    Bd.output(Bd.const(-1.0), P.KIND_INEQ)      # a constant entry as an output
+    return Bd.tape([[-1.5, 1.0]] * n, f"shared dag {seed}")
+
+
+RATIONAL = [W.OP_ADD, W.OP_SUB, W.OP_MUL, W.OP_DIV, W.OP_SQR, W.OP_NEG]
+ALL = RATIONAL + [W.OP_SQRT, W.OP_EXP, W.OP_LOG]
+
+
+@pytest.mark.parametrize("n,ops_kind,seed", [(1, "rational", 1), (3, "rational", 2), (5, "all", 3),
+                                              (8, "all", 4), (32, "rational", 5)])
+@pytest.mark.parametrize("grad_mode", ["adjoint", "forward"])
+def test_specialized_shared_subexpressions(n, ops_kind, seed, grad_mode):
+    """overlapping output cones, variable and constant outputs, equalities,
+    one to 32 variables: bit-identical to the interpreter, and to the oracle
+    on rational tapes"""
+    t = shared_dag(n, 30 if n < 32 else 20, 2, 1 if n > 1 else 0, RATIONAL if ops_kind == "rational" else ALL, seed)
+    nn = 9
+    boxes = W.bisection_frontier(t.root_box, nn, seed=seed)
+    splits = np.ones((nn, n), np.int32)
+    splits[:, : min(n, 3)] = 3
+    a, b = bound_both(t, boxes, splits, grad_mode=grad_mode)
+    for k in KEYS:
+        assert same_bits(a[k], b[k]), k
+    if ops_kind == "rational":
+        ref = oracle.bound_nodes(t, boxes, splits, grad_mode=grad_mode, tight=True)
+        for k in ("lb", "ub", "minlo", "maxhi"):
+            assert np.array_equal(b[k], ref[k]), k
