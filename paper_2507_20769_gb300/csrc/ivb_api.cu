@@ -12,15 +12,11 @@
 #include <vector>
 
 #include "../../include/ivb.h"
+#include "ivb_compile.h"
 #include "ivb_internal.h"
 #include "ivb_kernels.h"
 #include "ivb_problem.h"
 
-namespace ivb {
-std::string validate_tape(const ivb_tape* t);
-std::string compile_tape(const ivb_tape* t, HostProgram& P, std::vector<Ins>& ins, std::vector<RIns>& rins,
-                         std::vector<double>& consts);
-}  // namespace ivb
 
 using namespace ivb;
 

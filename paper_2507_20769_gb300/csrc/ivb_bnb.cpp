@@ -25,12 +25,10 @@
 #include <vector>
 
 #include "../../include/ivb.h"
+#include "ivb_compile.h"
 #include "ivb_host.h"
 #include "ivb_problem.h"
 
-namespace ivb {
-std::string validate_tape(const ivb_tape* t);
-}
 
 namespace {
 
@@ -90,10 +88,17 @@ extern "C" ivb_status ivb_propagate(const ivb_tape* tape, int32_t n_boxes, const
 
 extern "C" ivb_status ivb_bnb_solve(ivb_problem* p, int32_t n, const double* root, const ivb_bnb_options* o,
                                     ivb_bnb_result* res, void* stream_) {
-    if (!p || !root || !o || !res || n < 1 || n > IVB_MAX_VARS || n != p->n) return IVB_EINVAL;
-    if (o->batch < 1 || (o->split_mode == 0 && !o->splits) || (o->split_mode > 0 && o->target < 1) ||
-        o->propagate < 0)
+    if (!p) return IVB_EINVAL;
+    p->err.clear();
+    if (!root || !o || !res || n != p->n) {
+        p->err = "ivb_bnb_solve: root, options and result are required and n must equal the problem's n_vars";
         return IVB_EINVAL;
+    }
+    if (o->batch < 1 || (o->split_mode == 0 && !o->splits) || (o->split_mode > 0 && o->target < 1) ||
+        o->propagate < 0) {
+        p->err = "ivb_bnb_solve: batch >= 1, splits (split_mode 0) or target >= 1, propagate >= 0";
+        return IVB_EINVAL;
+    }
     cudaStream_t stream = (cudaStream_t)stream_;
     const ivb::HostTape& H = p->host;
     const int grad_mode = p->opt.grad_mode;
@@ -106,7 +111,10 @@ extern "C" ivb_status ivb_bnb_solve(ivb_problem* p, int32_t n, const double* roo
     double UB = INFINITY, lb_pruned = INFINITY;
     int64_t iters = 0, bounded = 0, subs = 0;
     const int cap = std::max(2 * o->batch, 1);
-    if (cap > p->max_nodes) return IVB_EINVAL;
+    if (cap > p->max_nodes) {
+        p->err = "ivb_bnb_solve: 2 * batch exceeds the problem's max_nodes";
+        return IVB_EINVAL;
+    }
 
     Batch bat[2];
     ivb_status st = IVB_OK;

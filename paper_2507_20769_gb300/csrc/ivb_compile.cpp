@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/ivb.h"
+#include "ivb_compile.h"
 #include "ivb_internal.h"
 
 namespace ivb {
