@@ -473,7 +473,8 @@ def bnb_config_study(configs, cap):
     """B&B to each configuration's gap: adjoint + batched (32 parents per
     iteration), then + constraint propagation, + CPU/GPU overlap, + the
     tape-specialised kernel (not for configuration 5, whose tapes are too
-    large to compile quickly). Configurations 3 and 5 split each node by the
+    large to compile quickly), and with MVF meet NIE and the filtered
+    objective. Configurations 3 and 5 split each node by the
     adaptive picker (2^15 and 2^18 subdomains per node)."""
     from paper_2507_20769_gb300 import ivb
     from paper_2507_20769_gb300 import workloads as W
@@ -487,6 +488,9 @@ def bnb_config_study(configs, cap):
                 ("+propagate+overlap", {}, dict(propagate=3, overlap=1))]
         if cfg != 5:
             arms.append(("+propagate+overlap+specialised", dict(specialize=1), dict(propagate=3, overlap=1)))
+        # the bound form: MVF intersected with the natural interval extension, filtered objective
+        arms.append(("+propagate+overlap+mvf_nie+filter", dict(form="mvf_nie", filter=1),
+                     dict(propagate=3, overlap=1)))
         for name, popts, bopts in arms:
             with ivb.Problem(t, grad_mode="adjoint", batched=1, **popts) as p:
                 r = p.bnb_solve(t.root_box, batch=32, eps_abs=wl.gap_abs, eps_rel=wl.gap_rel, time_limit=cap,
