@@ -309,9 +309,10 @@ ivb_status ivb_specialize_compile(const ivb_tape* tape, int32_t grad_mode, int32
                                   int32_t* spill_bytes, double* compile_seconds);
 
 /* Static count of the outward-rounded endpoint operations one subdomain
- * needs under the problem's gradient mode (the canonical formulas: value,
- * tangent or adjoint rules, Mean Value Form, decode; the kernel computes the
- * Mean Value Form for every form, so the form does not change it), per category
+ * needs under the problem's gradient mode and form (the canonical formulas:
+ * value, tangent or adjoint rules, Mean Value Form, decode; with the natural
+ * interval extension alone, IVB_FORM_NIE, the reduce kernels skip the
+ * gradients: decode, point sweep and value sweep only), per category
  * IVB_CNT_*: the algorithmic work of the bounding kernel per subdomain.
  * Interval products count two directed multiplies (sign-case selection). */
 enum {

@@ -321,7 +321,8 @@ cudaError_t specialize(ivb_problem* p, const std::vector<Ins>& ins, const std::v
                        const std::vector<double>& consts, int mode, std::string* msg) {
     const int emu = p->opt.emulate >= 0 ? p->opt.emulate : kJitDefaultEmulate;
     const bool compact = p->opt.specialize != 2;
-    const std::string src = jit_source(p->P, ins, rins, consts, mode, kJitBlockMax, kJitMinBlocks, emu, compact);
+    const std::string src =
+        jit_source(p->P, ins, rins, consts, mode, kJitBlockMax, kJitMinBlocks, emu, compact, p->opt.form);
     std::vector<char> cubin;
     std::string tables;
     double secs = 0.0;
@@ -771,7 +772,7 @@ extern "C" ivb_status ivb_specialize_compile(const ivb_tape* tape, int32_t grad_
     if (!e.empty()) return fail(nullptr, IVB_ENOTSUP, e);
     const int mode = grad_mode == IVB_GRAD_ADJOINT ? KM_ADJ_REDUCE : KM_FWD_REDUCE;
     const std::string src =
-        jit_source(P, ins, rins, consts, mode, kJitBlockMax, kJitMinBlocks, kJitDefaultEmulate, compact != 0);
+        jit_source(P, ins, rins, consts, mode, kJitBlockMax, kJitMinBlocks, kJitDefaultEmulate, compact != 0, 0);
     std::vector<char> cubin;
     std::string tables;
     int regs = 0, spill = 0;
@@ -800,7 +801,9 @@ extern "C" ivb_status ivb_eval_op(int32_t opcode, int64_t n, const double* x, co
 
 extern "C" ivb_status ivb_op_counts(const ivb_problem* p, int64_t counts[IVB_CNT_N]) {
     if (!p || !counts) return IVB_EINVAL;
-    const int64_t* c = p->opt.grad_mode == IVB_GRAD_ADJOINT ? p->P.cnt_adj : p->P.cnt_fwd;
+    const bool adj = p->opt.grad_mode == IVB_GRAD_ADJOINT;
+    const int64_t* c = p->opt.form == IVB_FORM_NIE ? (adj ? p->P.cnt_nie_adj : p->P.cnt_nie_fwd)
+                                                   : (adj ? p->P.cnt_adj : p->P.cnt_fwd);
     for (int i = 0; i < IVB_CNT_N; ++i) counts[i] = c[i];
     return IVB_OK;
 }

@@ -318,6 +318,13 @@ std::string compile_tape(const ivb_tape* t, HostProgram& P, std::vector<Ins>& in
         count_values(P.adj[o].fw_begin, P.adj[o].fw_count, P.cnt_adj);
         count_reverse(P.adj[o].rv_begin, P.adj[o].rv_count, P.cnt_adj);
     }
+    // form 1: decode, point sweep (for the centre upper bound) and the value sweep over X
+    for (int64_t* c : {P.cnt_nie_fwd, P.cnt_nie_adj}) {
+        c[RN] += 6LL * n;
+        count_values(P.pt_begin, P.pt_count, c);
+    }
+    count_values(P.tan_begin, P.tan_count, P.cnt_nie_fwd);
+    for (int o = 0; o < no; ++o) count_values(P.adj[o].fw_begin, P.adj[o].fw_count, P.cnt_nie_adj);
 
     // ---------------------------------------------------- frame layout
     FrameLayout& L = P.L;

@@ -95,6 +95,8 @@ struct HostProgram {
     int64_t op_hist[16] = {0};
     // directed endpoint operations per subdomain, per category (ivb.h IVB_CNT_*)
     int64_t cnt_fwd[8] = {0}, cnt_adj[8] = {0};
+    // the same for the natural interval extension alone (form 1): no gradients
+    int64_t cnt_nie_fwd[8] = {0}, cnt_nie_adj[8] = {0};
 };
 
 }  // namespace ivb

@@ -53,6 +53,7 @@ struct Gen {
     const RIns* rins;
     const double* consts;
     int n, no;
+    bool nie_only = false;   // form 1 (natural interval extension alone): no gradients needed
     std::string out;
 
     void line(int ind, const std::string& s) {
@@ -244,16 +245,21 @@ struct Gen {
     void finish(int ind, int o, const std::vector<std::string>& Gi, const std::string& nie) {
         line(ind, "{");
         const int j = ind + 1;
-        line(j, "iv mvf = fc" + S(o) + ";");
-        for (int i = 0; i < n; ++i) line(j, "mvf = mvf_term(mvf, " + Gi[i] + ", X" + S(i) + ", c" + S(i) + ");");
-        line(j, "F" + S(o) + " = final_form(P.form, mvf, " + nie + ");");
+        if (nie_only) {
+            line(j, "F" + S(o) + " = final_form(1, " + nie + ", " + nie + ");");
+        } else {
+            line(j, "iv mvf = fc" + S(o) + ";");
+            for (int i = 0; i < n; ++i) line(j, "mvf = mvf_term(mvf, " + Gi[i] + ", X" + S(i) + ", c" + S(i) + ");");
+            line(j, "F" + S(o) + " = final_form(P.form, mvf, " + nie + ");");
+        }
         line(j, "if (excludes_feasible(" + S(P.out_kind[o]) + "u, F" + S(o) + ")) cert = true;");
         if (o == P.obj) line(j, "obj_lo = F" + S(o) + ".lo;");
         line(ind, "}");
     }
 
-    std::string kernel(int mode, int block_max, int min_blocks, int emulate, bool compact) {
+    std::string kernel(int mode, int block_max, int min_blocks, int emulate, bool compact, int form) {
         out.clear();
+        nie_only = form == 1;
         line(0, "#define IVB_EMU " + S(emulate));
         if (compact) line(0, "#define IVB_HEAVY __noinline__");
         line(0, "typedef signed char int8_t; typedef unsigned char uint8_t;");
@@ -279,14 +285,20 @@ struct Gen {
                 for (int i = 0; i < n; ++i)
                     line(1, "const iv X" + S(i) + " = Xv[" + S(i) + "]; const double c" + S(i) + " = cv[" + S(i) + "];");
                 decls(1, "r", A.tape_records);
-                decls(1, "w", A.adj_slots);
-                decls(1, "g", n);
                 values(1, 'r', A.fw_begin, A.fw_count);
-                if (A.out_wslot >= 0) line(1, "w" + S(A.out_wslot) + " = one();");
-                reverse(1, A);
-                line(1, "iv mvf = fc;");
-                for (int i = 0; i < n; ++i) line(1, "mvf = mvf_term(mvf, g" + S(i) + ", X" + S(i) + ", c" + S(i) + ");");
-                line(1, "return final_form(form, mvf, " + val('r', (uint32_t)A.out_kind_ref, (uint32_t)A.out_ref) + ");");
+                const std::string nie = val('r', (uint32_t)A.out_kind_ref, (uint32_t)A.out_ref);
+                if (nie_only) {
+                    line(1, "return final_form(1, " + nie + ", " + nie + ");");
+                } else {
+                    decls(1, "w", A.adj_slots);
+                    decls(1, "g", n);
+                    if (A.out_wslot >= 0) line(1, "w" + S(A.out_wslot) + " = one();");
+                    reverse(1, A);
+                    line(1, "iv mvf = fc;");
+                    for (int i = 0; i < n; ++i)
+                        line(1, "mvf = mvf_term(mvf, g" + S(i) + ", X" + S(i) + ", c" + S(i) + ");");
+                    line(1, "return final_form(form, mvf, " + nie + ");");
+                }
                 line(0, "}");
             }
             line(0, "}  // namespace ivb");
@@ -342,9 +354,10 @@ struct Gen {
             const int e = d + 1;
             for (int k = 0; k < P.tan_slots; ++k) {
                 line(e, "iv t" + S(k) + " = zero();");
-                decls(e, ("t" + S(k) + "_").c_str(), n);
+                if (!nie_only) decls(e, ("t" + S(k) + "_").c_str(), n);
             }
-            tangents(e);
+            if (nie_only) values(e, 't', P.tan_begin, P.tan_count);
+            else tangents(e);
             for (int o = 0; o < no; ++o) {
                 const uint32_t kind = (uint32_t)P.tan_out_kind[o], ref = (uint32_t)P.tan_out_ref[o];
                 std::vector<std::string> G(n);
@@ -360,11 +373,13 @@ struct Gen {
                 line(d, "{  // output " + S(o) + ": forward sweep over its cone, then the reverse sweep");
                 const int e = d + 1;
                 decls(e, "r", A.tape_records);
-                decls(e, "w", A.adj_slots);
-                decls(e, "g", n);
                 values(e, 'r', A.fw_begin, A.fw_count);
-                if (A.out_wslot >= 0) line(e, "w" + S(A.out_wslot) + " = one();");
-                reverse(e, A);
+                if (!nie_only) {
+                    decls(e, "w", A.adj_slots);
+                    decls(e, "g", n);
+                    if (A.out_wslot >= 0) line(e, "w" + S(A.out_wslot) + " = one();");
+                    reverse(e, A);
+                }
                 std::vector<std::string> G(n);
                 for (int i = 0; i < n; ++i) G[i] = "g" + S(i);
                 finish(e, o, G, val('r', (uint32_t)A.out_kind_ref, (uint32_t)A.out_ref));
@@ -390,9 +405,9 @@ struct Gen {
 
 std::string jit_source(const HostProgram& P, const std::vector<Ins>& ins, const std::vector<RIns>& rins,
                        const std::vector<double>& consts, int mode, int block_max, int min_blocks, int emulate,
-                       bool compact) {
-    Gen g{P, ins.data(), rins.data(), consts.data(), P.n_vars, P.n_out, {}};
-    return g.kernel(mode, block_max, min_blocks, emulate, compact);
+                       bool compact, int form) {
+    Gen g{P, ins.data(), rins.data(), consts.data(), P.n_vars, P.n_out};
+    return g.kernel(mode, block_max, min_blocks, emulate, compact, form);
 }
 
 std::string jit_compile(const std::string& src, std::vector<char>& cubin, std::string& tables_name, double* seconds,

@@ -35,10 +35,11 @@ struct JitKernel {
     double compile_seconds = 0.0;
 };
 
-// CUDA C++ of the reduce-mode bounding kernel for this program
+// CUDA C++ of the reduce-mode bounding kernel for this program; form 1 (the
+// natural interval extension alone) leaves out the gradient sweeps
 std::string jit_source(const HostProgram& P, const std::vector<Ins>& ins, const std::vector<RIns>& rins,
                        const std::vector<double>& consts, int mode, int block_max, int min_blocks, int emulate,
-                       bool compact);
+                       bool compact, int form);
 // NVRTC for sm_103a; "" on success, else the compiler's message. With
 // `registers` / `spill_bytes` non-NULL, ptxas reports them (parsed from its log).
 std::string jit_compile(const std::string& src, std::vector<char>& cubin, std::string& tables_name, double* seconds,

@@ -261,15 +261,35 @@ __global__ void __launch_bounds__(512) k_bound(const KParams P) {
                 C.F.put(L.fc_base + 2 * o, load_val(C, G.pt_out_kind[o], G.pt_out_ref[o], L.phase_base, 2));
             C.point = false;
         }
-        // ---- Step 2b: gradient enclosures and the Mean Value Form, output by output
+        // ---- Step 2b: gradient enclosures and the Mean Value Form, output by output.
+        // With the natural interval extension alone (form 1) a reduce launch needs no
+        // gradients: only the value sweep over X_k.
+        const bool nie_only = (MODE == KM_FWD_REDUCE || MODE == KM_ADJ_REDUCE) && P.form == 1;
         bool cert_infeasible = false;
         double obj_lo = from_bits(0x7FF0000000000000LL);
         if (MODE == KM_FWD_REDUCE || MODE == KM_FWD_STORE) {
-            if (valid) run_tangents(G.ins + G.tan_begin, G.tan_count, C, L.phase_base, n);
+            if (valid) {
+                if (nie_only) run_values(G.ins + G.tan_begin, G.tan_count, C, L.phase_base);
+                else run_tangents(G.ins + G.tan_begin, G.tan_count, C, L.phase_base, n);
+            }
         }
         for (int o = 0; o < n_out; ++o) {
             iv F = zero(), Fc = zero();
-            if (valid) {
+            if (valid && nie_only) {
+                Fc = C.F.get(L.fc_base + 2 * o);
+                iv nie;
+                if (MODE == KM_FWD_REDUCE) {
+                    nie = load_val(C, G.tan_out_kind[o], G.tan_out_ref[o], L.phase_base, 2);
+                } else {
+                    const AdjProgram& A = G.adj[o];
+                    const int tb = L.phase_base + 2 * n + 2 * A.adj_slots;
+                    run_values(G.ins + A.fw_begin, A.fw_count, C, tb);
+                    nie = load_val(C, A.out_kind_ref, A.out_ref, tb, 2);
+                }
+                F = final_form(1, nie, nie);
+                if (excludes_feasible(G.out_kind[o], F)) cert_infeasible = true;
+                if (o == G.obj) obj_lo = F.lo;
+            } else if (valid) {
                 Fc = C.F.get(L.fc_base + 2 * o);
                 iv nie;
                 int gunit, gstride;  // gradient of this output: unit of G_0 and stride (0: constant/variable)

@@ -220,3 +220,23 @@ def test_specialized_shared_subexpressions(n, ops_kind, seed, grad_mode):
         ref = oracle.bound_nodes(t, boxes, splits, grad_mode=grad_mode, tight=True)
         for k in ("lb", "ub", "minlo", "maxhi"):
             assert np.array_equal(b[k], ref[k]), k
+
+
+@pytest.mark.parametrize("grad_mode", ["forward", "adjoint"])
+@pytest.mark.parametrize("spec", [0, 1])
+def test_nie_form_skips_gradients_and_matches_oracle(grad_mode, spec):
+    """with the natural interval extension alone the reduce kernels skip the
+    gradient sweeps; the bounds equal the oracle's NIE bounds bit for bit and
+    the reported work drops"""
+    t = rational_problem()
+    boxes, splits = ragged_batch(t, 29, seed=8)
+    with ivb.Problem(t, grad_mode=grad_mode, form="nie", specialize=spec) as p:
+        r = p.bound_nodes_ex(boxes, splits, want_hull=True)
+        nie_work = sum(p.op_counts().values())
+    with ivb.Problem(t, grad_mode=grad_mode, form="mvf") as p:
+        mvf_work = sum(p.op_counts().values())
+    ref = oracle.bound_nodes(t, boxes, splits, grad_mode=grad_mode, form="nie", tight=True)
+    for k in ("lb", "ub", "minlo", "maxhi"):
+        assert np.array_equal(r[k], ref[k]), k
+    assert np.array_equal(r["infeasible"].astype(bool), ref["infeasible"])
+    assert nie_work < 0.75 * mvf_work
