@@ -126,7 +126,8 @@ typedef struct {
                                   narrow FP64 pipe. Bitmask: 1 upper ends of
                                   products, 2 lower ends of products, 4 upper
                                   ends of sums and differences, 8 lower ends;
-                                  -1 (default): the library's choice       */
+                                  -1 (default): the library's choice, now 0
+                                  (no gain inside the bounding kernel)     */
 } ivb_options;
 
 typedef struct ivb_problem ivb_problem;
@@ -225,18 +226,19 @@ ivb_status ivb_pick_splits(int32_t n, const double* box, const double* ref_width
  * library's Subdomain Lower Bounding as the lower-bounding solver; a
  * measurement harness for time-to-gap. Each iteration pops up to `batch`
  * open nodes of lowest lower bound, bisects each along the dimension of
- * largest width relative to the root box and bounds all children in one
- * ivb_bound_nodes_ex call. Upper bounds (in place of the paper's local
- * solver): the certified centre-point values of ivb_bound_nodes_ex and, with
- * corner_ub = 1, a descent-corner point per iteration: for the child with the
+ * largest width relative to the root box, optionally tightens each child by
+ * constraint propagation (dropping children proven empty) and bounds the
+ * children in one call of the bounding path. Upper bounds (in place of the
+ * paper's local solver): the certified centre-point values of
+ * ivb_bound_nodes_ex and, with corner_ub = 1, a descent-corner point per
+ * iteration, evaluated rigorously on the host: for the child with the
  * smallest centre value, the corner of its box that the sign of the
  * objective's gradient enclosure over the box points to (centre where the
  * sign is unknown), else the midpoint between that corner and the centre,
- * evaluated rigorously and used when certified feasible. All children of an
- * iteration are bounded and the incumbent updated before any is dropped;
- * nodes are dropped when infeasible or lb >= UB - max(eps_abs, eps_rel |UB|);
- * the run stops when UB - min(open lb) is within that tolerance or a limit
- * is reached. */
+ * used when certified feasible. All children of an iteration are bounded
+ * and the incumbent updated before any is dropped; nodes are dropped when
+ * infeasible or lb >= UB - max(eps_abs, eps_rel |UB|); the run stops when
+ * UB - min(open lb) is within that tolerance or a limit is reached. */
 typedef struct {
     int32_t batch;             /* nodes popped per iteration (>= 1)         */
     int32_t split_mode;        /* 0: fixed `splits`; 1 + IVB_SPLIT_*: picker */
@@ -272,6 +274,10 @@ typedef struct {
 
 void ivb_bnb_options_default(ivb_bnb_options* o);
 
+/* root: host array [n][2]; n must equal the problem's n_vars. */
+ivb_status ivb_bnb_solve(ivb_problem* p, int32_t n, const double* root, const ivb_bnb_options* opt,
+                         ivb_bnb_result* result, void* cuda_stream);
+
 /* Constraint propagation on the host, no GPU needed: forward-backward bound
  * tightening (HC4-style projections through every operation) of n_boxes
  * boxes [n_boxes][n_vars][2] against the tape's inequalities (g <= 0),
@@ -282,9 +288,6 @@ void ivb_bnb_options_default(ivb_bnb_options* o);
  * kernels' interval rules. */
 ivb_status ivb_propagate(const ivb_tape* tape, int32_t n_boxes, const double* boxes, double ub,
                          int32_t passes, double* boxes_out, uint8_t* infeasible);
-/* root: host array [n][2]; n must equal the problem's n_vars. */
-ivb_status ivb_bnb_solve(ivb_problem* p, int32_t n, const double* root, const ivb_bnb_options* opt,
-                         ivb_bnb_result* result, void* cuda_stream);
 
 /* Tuning actually used by the batched path after autotuning (may be NULL):
  * block threads, blocks per SM, tile, frame in shared (0/1). */
@@ -300,9 +303,8 @@ ivb_status ivb_get_specialization(ivb_problem* p, int32_t* active, int32_t* regi
 
 /* Generate and compile (NVRTC, sm_103a) the tape-specialised kernel of a
  * tape without loading it -- needs no GPU; compact = 1 as for specialize = 1,
- * 0 as for specialize = 2.
- * Reports ptxas' registers per
- * thread and spill-store bytes, and the compile time (each may be NULL).
+ * 0 as for specialize = 2. Reports ptxas' registers per thread and
+ * spill-store bytes, and the compile time (each may be NULL).
  * IVB_ETAPE for an invalid tape, IVB_ENOTSUP (message in ivb_last_error(NULL))
  * when the program does not compile. */
 ivb_status ivb_specialize_compile(const ivb_tape* tape, int32_t grad_mode, int32_t compact, int32_t* registers,
