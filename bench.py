@@ -20,6 +20,7 @@ batch (weak scaling, no collective on the data path).
 from __future__ import annotations
 
 import argparse
+import platform
 import json
 import os
 import statistics
@@ -131,40 +132,68 @@ class ClockSampler:
 
 
 # --------------------------------------------------------- CPU oracle leg
-def oracle_rate(t, box, splits, seconds: float):
-    """oracle (as it stands, fast transcendental mode, adjoint gradients, all
-    host cores) on the first C subdomains of one workload node, C sized for
-    about `seconds` of CPU time; returns (subdomain-bounds/s, C, cores, secs)"""
+def cpu_model() -> str:
+    """the host CPU's model line from /proc/cpuinfo (AArch64 lists the part number)"""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            lines = fh.read().splitlines()
+    except OSError:
+        return platform.machine()
+    for key in ("model name", "Model name"):
+        for ln in lines:
+            if ln.startswith(key):
+                return ln.split(":", 1)[1].strip()
+    parts = sorted({ln.split(":", 1)[1].strip() for ln in lines if ln.startswith("CPU part")})
+    return f"{platform.machine()} (CPU part {', '.join(parts)})" if parts else platform.machine()
+
+
+def oracle_rate(t, boxes, splits, seconds: float):
+    """The oracle as it stands (fast exp/log mode, adjoint gradients, all host
+    cores) runs Steps 1-3 on whole workload nodes, as many as fit in about
+    `seconds`; then one core on 8192 subdomains of the first node. Returns
+    (subdomain-bounds/s, nodes, subdomains per node, cores, seconds,
+    subdomain-bounds/s on one core)."""
     import oracle
     cores = oracle.max_threads()
-    c0 = 256
+    S = int(np.prod(splits[0].astype(np.int64)))
     t0 = time.perf_counter()
-    oracle.enclose(t, box, splits, first=0, count=c0, grad_mode="adjoint", tight=False)
-    dt = max(time.perf_counter() - t0, 1e-4)
-    C = int(min(65536, max(c0, c0 * seconds / dt)))
+    oracle.bound_nodes(t, boxes[:1], splits[:1], grad_mode="adjoint", tight=False)
+    d1 = max(time.perf_counter() - t0, 1e-4)
+    k = int(min(len(boxes), max(1, round(seconds / d1))))
     t0 = time.perf_counter()
-    oracle.enclose(t, box, splits, first=0, count=C, grad_mode="adjoint", tight=False)
+    oracle.bound_nodes(t, boxes[:k], splits[:k], grad_mode="adjoint", tight=False)
     dt = time.perf_counter() - t0
-    return C * t.n_out / dt, C, cores, dt
+    one = min(8192, S)
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.enclose(t, boxes[0], splits[0], first=0, count=one, grad_mode="adjoint", tight=False)
+        d_one = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(cores)
+    return k * S * t.n_out / dt, k, S, cores, dt, one * t.n_out / d_one
 
 
 def run_reference(args, rank, world):
-    """--impl reference: the oracle on the host cores, same metric and workload"""
+    """--impl reference: the oracle on the host cores, same metric and workload;
+    each step bounds whole nodes (Steps 1-3), as many as fit its time share"""
     if rank != 0:
         return 0
     wl, t, boxes, splits = workload(0, 1, args.nodes)
     per_step = max(2.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
     import oracle
-    rate, C, cores, _ = oracle_rate(t, boxes[0], splits[0], per_step)
+    _, k, S, cores, _, _ = oracle_rate(t, boxes, splits, per_step)
     times = []
-    for k in range(args.warmup + args.steps):
+    for step in range(args.warmup + args.steps):
+        first = (step * k) % max(1, len(boxes) - k + 1)
         t0 = time.perf_counter()
-        oracle.enclose(t, boxes[k % len(boxes)], splits[0], first=0, count=C, grad_mode="adjoint", tight=False)
-        if k >= args.warmup:
+        oracle.bound_nodes(t, boxes[first:first + k], splits[first:first + k], grad_mode="adjoint", tight=False)
+        if step >= args.warmup:
             times.append(time.perf_counter() - t0)
     total = sum(times)
-    value = C * t.n_out * len(times) / total
-    sample = f"first {C} of the 65536 subdomains of one node per step (adjoint gradients, fast exp/log mode)"
+    value = k * S * t.n_out * len(times) / total
+    sample = (f"{k} whole nodes of {S} subdomains per step (Steps 1-3, adjoint gradients, fast exp/log mode); "
+              f"CPU: {cpu_model()}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -302,10 +331,11 @@ def main():
             "kernel": kernel_desc(p)}
 
     if rank == 0 and world == 1:
-        rate, C, cores, secs = oracle_rate(t, boxes[0], splits[0], args.cpu_seconds)
+        rate, k, S, cores, secs, rate1 = oracle_rate(t, boxes, splits, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"first {C} of the 65536 subdomains of node 0 ({secs:.1f} s; "
-                                          "adjoint gradients, fast exp/log mode)"}
+                                "sample": f"Steps 1-3 on {k} whole nodes of {S} subdomains ({secs:.1f} s; "
+                                          "adjoint gradients, fast exp/log mode)",
+                                "value_1core": rate1, "cpu": cpu_model()}
     if rank == 0 and world == 1 and args.specialize:
         line["interpreter"] = interpreter_compare(t, boxes_d, splits_d, out, flush, stream, subs_step, step_s)
     if rank == 0 and world == 1 and args.bnb:
