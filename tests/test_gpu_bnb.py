@@ -92,3 +92,24 @@ def test_bnb_config2_overlap_propagation_specialised():
     assert a["converged"] and b["converged"]
     assert b["lb"] <= a["ub"] and a["lb"] <= b["ub"]
     assert b["ub"] - b["lb"] <= wl.gap_rel * abs(b["ub"]) * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("grad_mode", ["forward", "adjoint"])
+def test_bnb_plain_path_with_host_additions(grad_mode):
+    """one launch per node (batched = 0) with propagation and overlap:
+    converges on the unit-disc problem and brackets -sqrt 2"""
+    t = P.constrained_toy("feasible")
+    with ivb.Problem(t, grad_mode=grad_mode, batched=0) as p:
+        r = p.bnb_solve(t.root_box, splits=[6, 6], batch=3, eps_abs=1e-6, eps_rel=0.0, max_nodes=100000,
+                        overlap=1, propagate=2)
+    assert r["converged"] and r["lb"] - 1e-12 <= -math.sqrt(2.0) <= r["ub"] + 1e-12
+
+
+def test_bnb_rejects_bad_arguments():
+    t = P.constrained_toy("feasible")
+    with ivb.Problem(t, max_nodes=8) as p:
+        with pytest.raises(ivb.IvbError) as e:
+            p.bnb_solve(t.root_box, splits=[6, 6], batch=16)      # 2 * batch > max_nodes
+        assert e.value.status == ivb.IVB_EINVAL and "max_nodes" in str(e.value)
+        with pytest.raises(ivb.IvbError):
+            p.bnb_solve(t.root_box, splits=[6, 6], batch=2, propagate=-1)
