@@ -53,6 +53,9 @@ def parse():
                     help="comma list of configurations (2, 3, 5) for a B&B time-to-gap study with the host "
                          "additions switched on one by one (minutes; off by default)")
     ap.add_argument("--bnb-config-cap", type=float, default=90.0, help="time cap per run of that study, seconds")
+    ap.add_argument("--oracle-bnb", type=float, default=0.0,
+                    help="> 0: also run the oracle-backed B&B (host cores) on configurations 1 and 2 with this "
+                         "time cap in seconds (off by default)")
     ap.add_argument("--specialize", type=int, default=1,
                     help="1: tape-specialised bounding kernel (NVRTC at problem creation); 0: tape interpreter")
     ap.add_argument("--patterns", type=int, default=1,
@@ -340,6 +343,8 @@ def main():
         line["interpreter"] = interpreter_compare(t, boxes_d, splits_d, out, flush, stream, subs_step, step_s)
     if rank == 0 and world == 1 and args.bnb:
         line["bnb"] = bnb_compare(t, wl, args.bnb_time)
+    if rank == 0 and world == 1 and args.oracle_bnb > 0:
+        line["oracle_bnb"] = oracle_bnb_study(args.oracle_bnb)
     if rank == 0 and world == 1 and args.bnb_configs:
         line["bnb_configs"] = bnb_config_study([int(c) for c in args.bnb_configs.split(",")], args.bnb_config_cap)
     if rank == 0 and world == 1 and args.patterns:
@@ -497,6 +502,21 @@ def bnb_compare(t, wl, cap):
     if c["converged"] and b["converged"]:
         res["speedup_time_to_gap_with_host_additions"] = b["seconds"] / c["seconds"]
     return res
+
+
+def oracle_bnb_study(cap):
+    """the oracle as the lower-bounding solver of the same B&B (one node per
+    iteration, fast exp/log mode, adjoint gradients), host cores, time-capped"""
+    import oracle
+    from paper_2507_20769_gb300 import workloads as W
+    out = []
+    for cfg in (1, 2):
+        wl = W.config_workload(cfg)
+        r = oracle.bnb(wl.tape, splits=wl.splits, eps_abs=wl.gap_abs, eps_rel=wl.gap_rel, grad_mode="adjoint",
+                       tight=False, time_limit=cap)
+        out.append({"config": cfg, "seconds": r["seconds"], "converged": r["converged"], "nodes": r["nodes"],
+                    "lb": r["lb"], "ub": r["ub"], "cores": oracle.max_threads(), "cpu": cpu_model()})
+    return out
 
 
 def bnb_config_study(configs, cap):
