@@ -147,7 +147,9 @@ def cpu_model() -> str:
             if ln.startswith(key):
                 return ln.split(":", 1)[1].strip()
     parts = sorted({ln.split(":", 1)[1].strip() for ln in lines if ln.startswith("CPU part")})
-    return f"{platform.machine()} (CPU part {', '.join(parts)})" if parts else platform.machine()
+    known = {"0xd4f": "Neoverse V2", "0xd40": "Neoverse V1", "0xd0c": "Neoverse N1", "0xd49": "Neoverse N2"}
+    names = [known.get(x.lower(), f"CPU part {x}") for x in parts]
+    return f"{platform.machine()} {', '.join(names)}" if names else platform.machine()
 
 
 def oracle_rate(t, boxes, splits, seconds: float):
