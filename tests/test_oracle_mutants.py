@@ -79,6 +79,15 @@ MUTANTS = [
     ("propagation cuts the objective at the wrong side",
      "else if (ub < INFINITY) { iv f = {-INFINITY, ub}; ok = meet_iv(z, f); }",
      "else if (ub < INFINITY) { iv f = {ub, INFINITY}; ok = meet_iv(z, f); }"),
+    ("propagation of a product multiplies instead of dividing",
+     "if (!straddles0(V[b])) ok = meet_iv(&V[a], iv_div(z, V[b]));",
+     "if (!straddles0(V[b])) ok = meet_iv(&V[a], iv_mul(z, V[b]));"),
+    ("propagation through a square root forgets to square",
+     "iv r = {z.lo > 0.0 ? prod_dn(z.lo, z.lo) : -INFINITY, prod_up(z.hi, z.hi)};",
+     "iv r = {z.lo > 0.0 ? z.lo : -INFINITY, z.hi};"),
+    ("propagation through exp applies exp instead of log",
+     "iv r = {z.lo > 0.0 ? log_dn(z.lo, tight) : -INFINITY, log_up(z.hi, tight)};",
+     "iv r = {exp_dn(z.lo, tight), exp_up(z.hi, tight)};"),
     ("adaptive partitioning grows the narrowest dimension",
      "                double v = rw[i] / out[i];\n                if (v > bestv) { bestv = v; best = i; }",
      "                double v = 1.0 / (rw[i] / out[i] + 1e-300);\n                if (v > bestv) { bestv = v; best = i; }"),
