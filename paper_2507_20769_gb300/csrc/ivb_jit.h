@@ -1,5 +1,12 @@
 // ivb_jit.h -- tape-specialised bounding kernels (generated CUDA C++,
 // compiled with NVRTC at problem creation); see ivb_jit.cpp.
+//
+// Variants of the generated source: compact (the default, option specialize
+// = 1) puts the point sweep and each output's adjoint sweeps in __noinline__
+// functions and calls the long primitives out of line, which halves the
+// compile time at the same speed; specialize = 2 inlines everything. With
+// form 1 (the natural interval extension alone) the gradient sweeps are left
+// out. Every variant is bit-identical to the interpreter.
 #pragma once
 #include <cuda_runtime.h>
 
