@@ -10,11 +10,16 @@
 // the correctly rounded result toward -inf or +inf. The results are the
 // correctly rounded directed values (identical to __ddiv_rd & co.); inputs
 // outside the fast path's exponent range, and results that are powers of two
-// (where the spacing of doubles changes), take the CUDA intrinsic.
+// (where the spacing of doubles changes), take the CUDA intrinsic. The sign of
+// the remainder comes from the integer pipe: the remainder is below 2^55 in
+// units of the last place of the significand product, so it equals the low
+// 64 bits of that product (one 64-bit integer multiply) read as a signed
+// integer, and no FP64 instruction is spent on it.
 //
 // exp and log (Tang's table-driven method, ACM TOMS 15(2) 1989 and 16(4)
-// 1990): exp(x) = 2^m 2^(j/512) e^r with |r| < 0.0008 and a degree-4
-// polynomial; log(x) = m ln2 - log(c_j) + log1p(x 2^-m c_j - 1) with 2048
+// 1990): exp(x) = 2^m 2^(j/512) e^r with |r| < 0.00082, e^r - 1 = r + r^2/2
+// in FP64 and the tail r^3/6 + r^4/24 + r^5/120 (below 2^-33) on the FP32
+// pipe, where 24 bits of it are enough; log(x) = m ln2 - log(c_j) + log1p(x 2^-m c_j - 1) with 2048
 // reciprocal centres c_j and a degree-5 polynomial. Large tables (read
 // through L1) buy short polynomials, i.e. fewer FP64 instructions. Tables are
 // double-double, computed on the host in extended precision. Error before
@@ -30,7 +35,7 @@ namespace ivb {
 // tables, in device memory of this module (filled by init_math_tables, or
 // copied from the library's tables into a tape-specialised module)
 constexpr int kExpTab = 512, kLogTab = 2048;
-struct ExpEntry { double hi, lo; };            // 2^(j/512) as hi + lo
+struct ExpEntry { double hi; float hi_f, lo_f; };   // 2^(j/512) = hi + lo; hi and lo rounded to float
 struct LogEntry { double c, hi, lo, pad; };    // reciprocal centre c_j, -log(c_j) as hi + lo
 struct MathTables {
     ExpEntry exp[kExpTab];
@@ -63,8 +68,21 @@ __device__ __forceinline__ double dn1(double y) {   // next toward -inf, y finit
     long long b = bits(y);
     return from_bits(b >= 0 ? b - 1 : b + 1);
 }
-__device__ __forceinline__ bool sgn_ge0(double x) { long long b = bits(x); return b >= 0 || b == (long long)0x8000000000000000ULL; }
-__device__ __forceinline__ bool sgn_le0(double x) { return bits(x) <= 0 || bits(x) == (long long)0x8000000000000000ULL; }
+
+// significand of a normal double as the integer in [2^52, 2^53)
+__device__ __forceinline__ unsigned long long sig53(double x) {
+    return ((unsigned long long)bits(x) & 0x000FFFFFFFFFFFFFULL) | 0x0010000000000000ULL;
+}
+// Remainder signs from the integer pipe. Write the normal doubles a, b, c as
+// A 2^ea, B 2^eb, C 2^ec with A, B, C their 53-bit significands (ea = biased
+// exponent Ea - 1075). Then c - a b = 2^(ea+eb) (C 2^s - A B) with
+// s = ec - ea - eb = Ec + 1075 - Ea - Eb. When c / (a b) is within 2^-50 of 1,
+// A B lies in [2^104, 2^106), s in 52..54 and |C 2^s - A B| < 2^56, so
+// C 2^s - A B equals the difference of the two products modulo 2^64 read as
+// a signed integer: a shift and one 64-bit multiply, exact, no FP64 instruction.
+__device__ __forceinline__ long long rem_sig(double a, double b, double c, int s) {
+    return (long long)((sig53(c) << s) - sig53(a) * sig53(b));
+}
 
 // Slow paths out of line: inlined, the compiler would start parts of them
 // speculatively on the fast path, which costs FP64 issue slots every call.
@@ -100,9 +118,11 @@ __device__ __forceinline__ double rcp_dir_pos(double y, bool up) {
         const double e = __fma_rn(-y, r0, 1.0);
         const double r = __fma_rn(r0, __fma_rn(e, e, e), r0);
         if (!mant_zero(r)) {
-            const double rho = __fma_rn(-y, r, 1.0);  // sign(1/y - r)
-            if (up) return (sgn_le0(rho)) ? r : up1(r);
-            return (sgn_ge0(rho)) ? r : dn1(r);
+            // sign(1 - y r); 1.0 has biased exponent 1023: s = 1023 + 1075 - Ey - Er
+            const int s = 2098 - bexp(y) - bexp(r);
+            const long long rho = rem_sig(y, r, 1.0, s);
+            if (up) return rho <= 0 ? r : up1(r);
+            return rho >= 0 ? r : dn1(r);
         }
     }
     return rcp_slow(y, up);
@@ -125,10 +145,13 @@ __device__ __forceinline__ double div_dir_pos(double x, double y, double r, bool
         if (x0) return x;                              // exact: +-0 / y = +-0 for y > 0
         const double q0 = x * r;
         const double q = __fma_rn(__fma_rn(-y, q0, x), r, q0);   // within 0.5 ulp + 2^-80 relative
-        if (!mant_zero(q)) {
-            const double rho = __fma_rn(-y, q, x);     // sign(x/y - q)
-            if (up) return sgn_le0(rho) ? q : up1(q);
-            return sgn_ge0(rho) ? q : dn1(q);
+        const int s = Ex + 1075 - Ey - bexp(q);        // 52..54 for q near x / y
+        if (!mant_zero(q) && (unsigned)(s - 48) <= 8u) {
+            // sign(x/y - q) = sign(x - y q): |X 2^s - Y Q| for the magnitudes, sign of x applied
+            const long long t = rem_sig(y, q, x, s);
+            const long long rho = bits(x) < 0 ? -t : t;
+            if (up) return rho <= 0 ? q : up1(q);
+            return rho >= 0 ? q : dn1(q);
         }
     }
     return div_slow(x, y, up);
@@ -162,10 +185,11 @@ __device__ __forceinline__ double sqrt_dir(double x, bool up) {
         // last step: the remainder x - g^2 is < 2^-40 x, so the seed-accurate 1/(2 sqrt x)
         // (2^-21) leaves < 2^-62 relative: within 0.5 ulp + 2^-62 after one rounding
         g = __fma_rn(__fma_rn(-g, g, x), hh, g);
-        if (!mant_zero(g)) {
-            const double d = __fma_rn(-g, g, x);     // sign(sqrt(x) - g)
-            if (up) return sgn_le0(d) ? g : up1(g);
-            return sgn_ge0(d) ? g : dn1(g);
+        const int s = E + 1075 - 2 * bexp(g);          // 52..54 for g near sqrt(x)
+        if (!mant_zero(g) && (unsigned)(s - 48) <= 8u) {
+            const long long d = rem_sig(g, g, x, s);   // sign(x - g^2) = sign(sqrt(x) - g)
+            if (up) return d <= 0 ? g : up1(g);
+            return d >= 0 ? g : dn1(g);
         }
     }
     return sqrt_slow(x, up);
@@ -184,7 +208,34 @@ __device__ __forceinline__ double int_to_double(int k) {
     return from_bits(a != 0u ? (long long)b : 0LL);
 }
 
-// exp(x) for |x| <= 700 (fast path): one final rounding plus < 2^-58 relative
+// float nearest to a double v with 2^-126 <= |v| < 2^127 (ties away from
+// zero), 0 for smaller |v|; integer pipe only
+__device__ __forceinline__ float f32_near(double v) {
+    const long long b = bits(v);
+    const int E = (int)((b >> 52) & 0x7FF);
+    const long long m = (b & 0x7FFFFFFFFFFFFFFFLL) + (1LL << 28);   // round the 29 dropped bits
+    const int fb = (int)((m >> 29) - ((long long)(1023 - 127) << 23));
+    return __int_as_float(E > 1023 - 127 ? (fb | (int)((b >> 32) & 0x80000000)) : 0);
+}
+// the double equal to a normal float (0 for zero and subnormal floats); integer pipe only
+__device__ __forceinline__ double f64_of(float f) {
+    const unsigned fb = (unsigned)__float_as_int(f);
+    const unsigned e = (fb >> 23) & 0xFFu;
+    const unsigned long long db = ((unsigned long long)(fb >> 31) << 63) |
+                                  ((unsigned long long)(e + (1023u - 127u)) << 52) |
+                                  ((unsigned long long)(fb & 0x7FFFFFu) << 29);
+    return from_bits(e != 0u ? (long long)db : 0LL);
+}
+
+// exp(x) for |x| <= 700 (fast path). With k = round(x 512/ln2) (within 0.6 of
+// x 512/ln2), j = k mod 512, m = k div 512 and r = x - k ln2/512 (|r| <= 0.6 ln2/512
+// < 0.00082): exp(x) = 2^m 2^(j/512) (1 + r + r^2/2 + tau), tau = r^3/6 + r^4/24 +
+// r^5/120 + ... < 2^-33.3. r + r^2/2 is one FP64 fma (r/2 is exact); tau and its
+// product with the table entry go on the FP32 pipe: 24-bit arithmetic leaves tau
+// within 2^-21 relative, i.e. 2^-54.3 absolute, and tl + th tau within 2^-53.3.
+// Error before the final rounding below 2^-53.7 of the result (one final rounding
+// on top; two-step outward widening needs less than 0.75 ulp of it at powers of
+// two and 1.5 ulp elsewhere).
 __device__ __forceinline__ double exp_core(double x, bool* ok) {
     const long long b = bits(x);
     const int E = (int)((b >> 52) & 0x7FF);
@@ -200,14 +251,19 @@ __device__ __forceinline__ double exp_core(double x, bool* ok) {
     const double C1 = 0x1.62e42ff000000p-10, C2 = -0x1.718432a1b0e26p-44;
     double r = __fma_rn(-kd, C1, x);
     r = __fma_rn(-kd, C2, r);
-    // p = e^r - 1, |r| < 0.0008: truncation below 2^-58
-    double u = __fma_rn(r, 1.0 / 24.0, 1.0 / 6.0);
-    u = __fma_rn(r, u, 0.5);
-    u = __fma_rn(r, u, 1.0);
-    const double p = r * u;
+    // FP32: tau = r^3 (1/6 + r/24 + r^2/120)
+    const float rf = f32_near(r);
+    float q = __fmaf_rn(rf, 1.0f / 120.0f, 1.0f / 24.0f);
+    q = __fmaf_rn(rf, q, 1.0f / 6.0f);
+    const float tau = __fmul_rn(__fmul_rn(__fmul_rn(rf, rf), rf), q);
     const int j = k & (kExpTab - 1), m = k >> 9;
-    const double th = g_math.exp[j].hi, tl = g_math.exp[j].lo;
-    const double y = th + __fma_rn(th, p, tl);       // 2^(j/512) (1 + p), one final rounding
+    const ExpEntry T = g_math.exp[j];
+    const double e = f64_of(__fmaf_rn(T.hi_f, tau, T.lo_f));       // tl + th tau
+    // FP64: 2^(j/512) (1 + r + r^2/2) + e with one final rounding
+    const long long rb = bits(r);
+    const double h = ((rb >> 52) & 0x7FF) >= 2 ? from_bits(rb - (1LL << 52)) : 0.0;   // r / 2
+    const double p2 = __fma_rn(r, h, r);
+    const double y = T.hi + __fma_rn(T.hi, p2, e);
     return from_bits(bits(y) + ((long long)m << 52));
 }
 

@@ -592,6 +592,7 @@ cudaError_t run_own_probe(int which, double* out, int grid, int block, int iters
 
 // exp/log tables in extended precision on the host (long double: 64-bit
 // significand on x86-64, binary128 on AArch64), split into double hi + lo
+// (the exp table keeps hi, and hi and lo rounded to float)
 cudaError_t math_tables_address(void** ptr, size_t* bytes) {
     *bytes = sizeof(MathTables);
     return cudaGetSymbolAddress(ptr, g_math);
@@ -607,7 +608,8 @@ cudaError_t init_math_tables() {
     for (int j = 0; j < kExpTab; ++j) {
         const long double v = exp2l((long double)j / kExpTab);
         h.exp[j].hi = (double)v;
-        h.exp[j].lo = (double)(v - (long double)h.exp[j].hi);
+        h.exp[j].hi_f = (float)h.exp[j].hi;
+        h.exp[j].lo_f = (float)(v - (long double)h.exp[j].hi);
     }
     const long double T = kLogTab;
     for (int j = 0; j < kLogTab; ++j) {

@@ -96,6 +96,26 @@ def test_division_exact_and_binade_cases():
             assert np.array_equal(R, oracle.iv_op(W.OP_DIV, sgn * X, Y))
 
 
+def test_sqrt_and_reciprocal_exact_and_neighbouring_cases():
+    """square roots of exact squares (zero remainder) and of their neighbours
+    (remainder of one unit), reciprocals of products of powers of two and
+    short odd integers and of their neighbours: the cases where the sign of
+    the remainder decides the directed result"""
+    rng = np.random.default_rng(21)
+    g = random_doubles(rng, 30000, -400, 400, sign=False)
+    g = (g.view(np.int64) & ~np.int64(0x7FFFFFF)).view(np.float64)      # 26-bit significands: g^2 exact
+    sq = g * g
+    x = np.concatenate([sq, np.nextafter(sq, 0.0), np.nextafter(sq, np.inf)])
+    X = np.stack([x, x], 1)
+    assert np.array_equal(gpu(W.OP_SQRT, X), oracle.iv_op(W.OP_SQRT, X))
+    odd = rng.integers(1, 1 << 20, 30000) * 2 + 1
+    y = np.ldexp(odd.astype(np.float64), rng.integers(-300, 300, odd.size))
+    y = np.concatenate([y, np.nextafter(y, 0.0), np.nextafter(y, np.inf), np.ldexp(1.0, rng.integers(-900, 900, 100))])
+    for sgn in (1.0, -1.0):
+        Y = np.stack([sgn * y, sgn * y], 1)
+        assert np.array_equal(gpu(RECIP, Y), oracle.iv_op(RECIP, Y))
+
+
 @pytest.mark.parametrize("opcode", [W.OP_SQR, W.OP_SQRT, RECIP, W.OP_NEG])
 def test_unary_ops_bit_exact(opcode):
     rng = np.random.default_rng(50 + opcode)
