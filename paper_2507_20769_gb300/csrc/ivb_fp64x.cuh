@@ -11,7 +11,7 @@
 // correctly rounded directed values (identical to __ddiv_rd & co.); inputs
 // outside the fast path's exponent range, and results that are powers of two
 // (where the spacing of doubles changes), take the CUDA intrinsic. The sign of
-// the remainder comes from the integer pipe: the remainder is below 2^55 in
+// the remainder comes from the integer pipe: the remainder is below 2^56 in
 // units of the last place of the significand product, so it equals the low
 // 64 bits of that product (one 64-bit integer multiply) read as a signed
 // integer, and no FP64 instruction is spent on it.
@@ -19,12 +19,14 @@
 // exp and log (Tang's table-driven method, ACM TOMS 15(2) 1989 and 16(4)
 // 1990): exp(x) = 2^m 2^(j/512) e^r with |r| < 0.00082, e^r - 1 = r + r^2/2
 // in FP64 and the tail r^3/6 + r^4/24 + r^5/120 (below 2^-33) on the FP32
-// pipe, where 24 bits of it are enough; log(x) = m ln2 - log(c_j) + log1p(x 2^-m c_j - 1) with 2048
-// reciprocal centres c_j and a degree-5 polynomial. Large tables (read
-// through L1) buy short polynomials, i.e. fewer FP64 instructions. Tables are
-// double-double, computed on the host in extended precision. Error before
-// widening below 1.5 ulp of the result; the interval ends are then moved two
-// neighbour steps outward, which encloses the true value.
+// pipe, where 24 bits of it are enough; log(x) = m ln2 - log(c_j) +
+// log1p(x 2^-m c_j - 1) with 2048 reciprocal centres c_j and a degree-5
+// polynomial whose r^4 and r^5 terms come from the FP32 pipe. Large tables
+// (read through L1) buy short polynomials, i.e. fewer FP64 instructions.
+// Tables are computed on the host in extended precision. Error before the
+// final rounding below 0.6 ulp of the result; the interval ends are then
+// moved two neighbour steps outward, which covers at least one ulp (of the
+// binade above) on each side, so they enclose the true value.
 #pragma once
 #ifndef __CUDACC_RTC__
 #include <cstdint>
@@ -103,19 +105,36 @@ __device__ __forceinline__ double rcp_seed(double y) {
     return from_bits(db);
 }
 
+// 1 - y r0 for a seed r0 of 24 significant bits with |1 - y r0| < 2^-20, from the
+// integer pipe. With Y, R0 the significands (R0 of 24 bits), y r0 = Y R0 2^-K with
+// K = 2121 - Ey - Er >= 75 and |2^K - Y R0| < 2^57, so 2^K - Y R0 is minus the
+// low 64 bits of Y R0; it becomes a double by bit assembly with truncation
+// (relative error below 2^-52, which the refinements below tolerate).
+__device__ __forceinline__ double one_minus_prod24(double y, double r0) {
+    const unsigned long long Y = sig53(y), R = sig53(r0) >> 29;
+    const long long D = -(long long)(Y * R);
+    const unsigned long long A = D < 0 ? 0ULL - (unsigned long long)D : (unsigned long long)D;
+    const int lz = __clzll((long long)A);
+    const unsigned long long N = A << (lz & 63);
+    const int K = 2121 - bexp(y) - bexp(r0);
+    const unsigned long long b = ((unsigned long long)(D < 0) << 63) |
+                                 ((unsigned long long)(1023 + 63 - lz - K) << 52) | ((N >> 11) & 0x000FFFFFFFFFFFFFULL);
+    return from_bits(A != 0ULL ? (long long)b : 0LL);
+}
+
 // fast-path exponent window: products, quotients and remainders stay normal
 __device__ __forceinline__ bool safe_e(int E) { return E >= 64 && E <= 1980; }
 
 // ---------------------------------------------------------------- reciprocal
 // correctly rounded 1/y toward -inf (up = false) or +inf (up = true), y > 0.
-// With e = 1 - y r0 (|e| < 2^-21, computed with one rounding), 1/y =
+// With e = 1 - y r0 (|e| < 2^-21, from the integer pipe), 1/y =
 // r0 / (1 - e) = r0 (1 + e + e^2 + e^3 + ...): r0 + r0 (e + e^2) leaves e^3 <
 // 2^-63, so one rounding puts r within 0.5 ulp + 2^-62 relative of 1/y, and the
 // exact residual 1 - y r picks the directed neighbour.
 __device__ __forceinline__ double rcp_dir_pos(double y, bool up) {
     if (safe_e(bexp(y))) {
         const double r0 = rcp_seed(y);
-        const double e = __fma_rn(-y, r0, 1.0);
+        const double e = one_minus_prod24(y, r0);
         const double r = __fma_rn(r0, __fma_rn(e, e, e), r0);
         if (!mant_zero(r)) {
             // sign(1 - y r); 1.0 has biased exponent 1023: s = 1023 + 1075 - Ey - Er
@@ -134,7 +153,7 @@ __device__ __forceinline__ double rcp_dir_pos(double y, bool up) {
 __device__ __forceinline__ double rcp_refined(double y) {
     if (!safe_e(bexp(y))) return 0.0;
     const double r = rcp_seed(y);
-    return __fma_rn(r, __fma_rn(-y, r, 1.0), r);
+    return __fma_rn(r, one_minus_prod24(y, r), r);
 }
 
 // correctly rounded x/y toward -inf or +inf, y > 0, given r = rcp_refined(y)
