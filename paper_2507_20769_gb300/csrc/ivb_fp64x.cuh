@@ -300,12 +300,21 @@ __device__ __forceinline__ double log_core(double x, bool* ok) {
     const double y = from_bits(yb);
     const LogEntry& T = g_math.log[j];
     const double r = __fma_rn(y, T.c, -1.0);          // |r| <= 2^-11
-    // log1p(r) = r + r^2 P(r), P to degree 3: relative truncation below 2^-57
-    // (next to 1, where r = y - 1 exactly and the result is about r) and below
-    // 2^-62 elsewhere, where the result is at least 2^-11.3 in magnitude
-    double P = __fma_rn(r, 0.2, -0.25);
-    P = __fma_rn(r, P, 1.0 / 3.0);
-    P = __fma_rn(r, P, -0.5);
+    // log1p(r) = r + r^2 P(r), P = -1/2 + r/3 - r^2/4 + r^3/5: relative truncation
+    // below 2^-57 (next to 1, where r = y - 1 exactly and the result is about r)
+    // and below 2^-62 elsewhere, where the result is at least 2^-11.3 in
+    // magnitude. delta = r^2 (-1/4 + r/5) is <= 0 and below 2^-22 in magnitude,
+    // so it goes on the FP32 pipe (24 bits of it are enough: its error reaches
+    // the result multiplied by r^2), and C = -1/2 + delta is assembled exactly on
+    // the integer pipe from delta cut to units of 2^-53: P = r/3 + C, one FP64 fma.
+    const float rf = f32_near(r);
+    const float delta = __fmul_rn(__fmul_rn(rf, rf), __fmaf_rn(rf, 0.2f, -0.25f));
+    const int db = __float_as_int(delta) & 0x7FFFFFFF;
+    const int sh = (db >> 23) - 127 + 30;              // |delta| = M 2^(sh - 53), M of 24 bits
+    const long long M = (long long)((db & 0x7FFFFF) | 0x800000);
+    const long long D = db == 0 ? 0LL : (sh >= 0 ? (M << sh) : (sh > -40 ? (M >> -sh) : 0LL));
+    const double C = from_bits((long long)0xBFE0000000000000ULL | D);   // -(1/2 + D 2^-53)
+    const double P = __fma_rn(r, 1.0 / 3.0, C);
     const double md = int_to_double(m);
     // ln2 = LN2_HI + LN2_LO: LN2_HI is ln2 rounded to 42 significant bits (m LN2_HI is
     // exact for |m| < 2^11), LN2_LO the remainder rounded to nearest
