@@ -316,7 +316,10 @@ ivb_status ivb_specialize_compile(const ivb_tape* tape, int32_t grad_mode, int32
  * interval extension alone, IVB_FORM_NIE, the reduce kernels skip the
  * gradients: decode, point sweep and value sweep only), per category
  * IVB_CNT_*: the algorithmic work of the bounding kernel per subdomain.
- * Interval products count two directed multiplies (sign-case selection). */
+ * Interval products count two directed multiplies (sign-case selection); a
+ * product added to an accumulator (adjoint accumulation, tangent rules, the
+ * Mean Value Form sum) is one fused multiply-add per end, counted as a
+ * multiply with no separate add. */
 enum {
     IVB_CNT_ADDSUB = 0, IVB_CNT_MUL = 1, IVB_CNT_DIV = 2, IVB_CNT_RCP = 3,
     IVB_CNT_SQRT = 4, IVB_CNT_EXP = 5, IVB_CNT_LOG = 6, IVB_CNT_RN = 7, IVB_CNT_N = 8
@@ -347,14 +350,18 @@ ivb_status ivb_fp64_probe(int32_t which, int32_t iters, double* lane_ops_per_s);
  * (the natural interval extension of an intrinsic, Section 2.2, with this
  * library's outward rounding) on n intervals: x, y, r are DEVICE arrays
  * [n][2]; opcode is a binary or unary tape opcode, IVB_EVAL_RECIP for the
- * interval reciprocal 1/x, or IVB_EVAL_EMU_* for +, -, *, sqr with every
- * endpoint operation done by the integer-pipe emulation (option `emulate`).
+ * interval reciprocal 1/x, IVB_EVAL_EMU_* for +, -, *, sqr with every
+ * endpoint operation done by the integer-pipe emulation (option `emulate`),
+ * or IVB_EVAL_FMA for r + x*y with one directed rounding per end (the fused
+ * accumulation of the adjoint sweep, the tangent rules and the Mean Value
+ * Form sum): r holds the addend on entry and the result on return.
  * Enqueued on cuda_stream. */
 #define IVB_EVAL_RECIP 100
 #define IVB_EVAL_EMU_ADD 101
 #define IVB_EVAL_EMU_SUB 102
 #define IVB_EVAL_EMU_MUL 103
 #define IVB_EVAL_EMU_SQR 104
+#define IVB_EVAL_FMA 105
 ivb_status ivb_eval_op(int32_t opcode, int64_t n, const double* x, const double* y, double* r,
                        void* cuda_stream);
 

@@ -219,6 +219,15 @@ def iv_op(opcode: int, x, y=None, tight: bool = True):
     return r
 
 
+def iv_fma(x, y, acc):
+    """acc + x*y with one directed rounding per end, on arrays of intervals [..., 2]"""
+    x = _f64(x).reshape(-1, 2)
+    y = _f64(np.broadcast_to(np.asarray(y, dtype=np.float64).reshape(-1, 2), x.shape))
+    r = _f64(np.broadcast_to(np.asarray(acc, dtype=np.float64).reshape(-1, 2), x.shape)).copy()
+    lib().orc_iv_op(105, x.shape[0], _p(x), _p(y), 1, _p(r))
+    return r
+
+
 def pick_splits(box, target: int, strategy: str = "adaptive", ref=None):
     box = _f64(box).reshape(-1, 2)
     n = box.shape[0]

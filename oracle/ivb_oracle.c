@@ -100,6 +100,23 @@ DIRECTED2(mul_up, FE_UPWARD, vx * vy)
 DIRECTED2(div_dn, FE_DOWNWARD, vx / vy)
 DIRECTED2(div_up, FE_UPWARD, vx / vy)
 
+/* fused multiply-add rounded once, toward -inf / +inf: RD(x y + z), RU(x y + z)
+ * (C99 fma is correctly rounded in the current rounding mode) */
+static double fma_dn(double x, double y, double z) {
+    volatile double vx = x, vy = y, vz = z, r;
+    fesetround(FE_DOWNWARD);
+    r = fma(vx, vy, vz);
+    fesetround(FE_TONEAREST);
+    return r;
+}
+static double fma_up(double x, double y, double z) {
+    volatile double vx = x, vy = y, vz = z, r;
+    fesetround(FE_UPWARD);
+    r = fma(vx, vy, vz);
+    fesetround(FE_TONEAREST);
+    return r;
+}
+
 static double sqrt_dn(double x) {
     volatile double vx = x, r;
     fesetround(FE_DOWNWARD);
@@ -119,6 +136,11 @@ static double sqrt_up(double x) {
  * factors stand for sets of reals, so a zero factor gives an exact zero */
 static double prod_dn(double x, double y) { return (x == 0.0 || y == 0.0) ? 0.0 : mul_dn(x, y); }
 static double prod_up(double x, double y) { return (x == 0.0 || y == 0.0) ? 0.0 : mul_up(x, y); }
+
+/* z + x y with one rounding and the same convention: a zero factor adds an
+ * exact zero */
+static double fprod_dn(double x, double y, double z) { return (x == 0.0 || y == 0.0) ? add_dn(z, 0.0) : fma_dn(x, y, z); }
+static double fprod_up(double x, double y, double z) { return (x == 0.0 || y == 0.0) ? add_up(z, 0.0) : fma_up(x, y, z); }
 
 static double min2(double x, double y) { return x < y ? x : y; }
 static double max2(double x, double y) { return x > y ? x : y; }
@@ -176,6 +198,25 @@ static iv iv_mul(iv x, iv y) {
     iv r;
     r.lo = min4(prod_dn(x.lo, y.lo), prod_dn(x.lo, y.hi), prod_dn(x.hi, y.lo), prod_dn(x.hi, y.hi));
     r.hi = max4(prod_up(x.lo, y.lo), prod_up(x.lo, y.hi), prod_up(x.hi, y.lo), prod_up(x.hi, y.hi));
+    return r;
+}
+
+/* min / max that skip NaN (NaN only when every argument is NaN) */
+static double minnn(double x, double y) { return isnan(x) ? y : (isnan(y) ? x : (x < y ? x : y)); }
+static double maxnn(double x, double y) { return isnan(x) ? y : (isnan(y) ? x : (x > y ? x : y)); }
+
+/* acc + x y with one directed rounding per end (a fused multiply-add, which
+ * the adjoint accumulation, the tangent rules and the Mean Value Form sum use):
+ * lo = RD(acc.lo + min of the four endpoint products), hi = RU(acc.hi + max).
+ * RD and RU are monotone, so the min (max) of the four fused candidates is
+ * that value. A candidate is NaN only where an infinite addend meets the
+ * opposite infinite product; such candidates are skipped unless all are NaN. */
+static iv iv_fma(iv x, iv y, iv acc) {
+    iv r;
+    r.lo = minnn(minnn(fprod_dn(x.lo, y.lo, acc.lo), fprod_dn(x.lo, y.hi, acc.lo)),
+                 minnn(fprod_dn(x.hi, y.lo, acc.lo), fprod_dn(x.hi, y.hi, acc.lo)));
+    r.hi = maxnn(maxnn(fprod_up(x.lo, y.lo, acc.hi), fprod_up(x.lo, y.hi, acc.hi)),
+                 maxnn(fprod_up(x.hi, y.lo, acc.hi), fprod_up(x.hi, y.hi, acc.hi)));
     return r;
 }
 
@@ -251,8 +292,10 @@ static void value_sweep(const tape_t* T, const iv* X, iv* V, int tight) {
 }
 
 /* Tangent-mode interval AD (Section 3.2): D[t*n+d] encloses d(node t)/dx_d
- * over X, one vector sweep for all n directions. Local rules:
- *   mul:  da*B + A*db            div:  (da - V*db) * (1/B)
+ * over X, one vector sweep for all n directions. Local rules ("+ ... fused":
+ * the product is added with one rounding per end, iv_fma):
+ *   mul:  da*B + A*db, the second product fused
+ *   div:  (da + (-V)*db fused) * (1/B)
  *   sqr:  (2A)*da                sqrt: da * (1/(2V))
  *   exp:  V*da                   log:  da * (1/A)                          */
 static void tangent_sweep(const tape_t* T, const iv* V, iv* D) {
@@ -270,11 +313,11 @@ static void tangent_sweep(const tape_t* T, const iv* V, iv* D) {
         case OP_SUB: for (int d = 0; d < n; ++d) Dt[d] = iv_sub(Da[d], Db[d]); break;
         case OP_NEG: for (int d = 0; d < n; ++d) Dt[d] = iv_neg(Da[d]); break;
         case OP_MUL:
-            for (int d = 0; d < n; ++d) Dt[d] = iv_add(iv_mul(Da[d], V[b]), iv_mul(V[a], Db[d]));
+            for (int d = 0; d < n; ++d) Dt[d] = iv_fma(V[a], Db[d], iv_mul(Da[d], V[b]));
             break;
         case OP_DIV:
             R = iv_recip(V[b]);
-            for (int d = 0; d < n; ++d) Dt[d] = iv_mul(iv_sub(Da[d], iv_mul(V[t], Db[d])), R);
+            for (int d = 0; d < n; ++d) Dt[d] = iv_mul(iv_fma(iv_neg(V[t]), Db[d], Da[d]), R);
             break;
         case OP_SQR:
             R = iv_twice(V[a]);
@@ -298,7 +341,8 @@ static void tangent_sweep(const tape_t* T, const iv* V, iv* D) {
 
 /* Reverse-mode interval AD for output node `out`: A[t] accumulates the
  * adjoint of node t, processed from `out` down to node 0; for each node the
- * first operand is updated before the second. G[i] encloses df/dx_i over X. */
+ * first operand is updated before the second, a product contribution with
+ * one rounding per end (iv_fma). G[i] encloses df/dx_i over X. */
 static void adjoint_sweep(const tape_t* T, const iv* V, int out, iv* A, iv* G) {
     const int n = T->n_vars;
     for (int t = 0; t <= out; ++t) A[t] = ZERO;
@@ -315,18 +359,18 @@ static void adjoint_sweep(const tape_t* T, const iv* V, int out, iv* A, iv* G) {
         case OP_SUB: A[a] = iv_add(A[a], w); A[b] = iv_sub(A[b], w); break;
         case OP_NEG: A[a] = iv_sub(A[a], w); break;
         case OP_MUL:
-            A[a] = iv_add(A[a], iv_mul(w, V[b]));
-            A[b] = iv_add(A[b], iv_mul(w, V[a]));
+            A[a] = iv_fma(w, V[b], A[a]);
+            A[b] = iv_fma(w, V[a], A[b]);
             break;
         case OP_DIV:
             R = iv_recip(V[b]);
-            A[a] = iv_add(A[a], iv_mul(w, R));
-            A[b] = iv_sub(A[b], iv_mul(iv_mul(w, V[t]), R));
+            A[a] = iv_fma(w, R, A[a]);
+            A[b] = iv_fma(iv_neg(iv_mul(w, V[t])), R, A[b]);
             break;
-        case OP_SQR: A[a] = iv_add(A[a], iv_mul(w, iv_twice(V[a]))); break;
-        case OP_SQRT: A[a] = iv_add(A[a], iv_mul(w, iv_recip_pos(iv_twice(V[t])))); break;
-        case OP_EXP: A[a] = iv_add(A[a], iv_mul(w, V[t])); break;
-        case OP_LOG: A[a] = iv_add(A[a], iv_mul(w, iv_recip_pos(V[a]))); break;
+        case OP_SQR: A[a] = iv_fma(w, iv_twice(V[a]), A[a]); break;
+        case OP_SQRT: A[a] = iv_fma(w, iv_recip_pos(iv_twice(V[t])), A[a]); break;
+        case OP_EXP: A[a] = iv_fma(w, V[t], A[a]); break;
+        case OP_LOG: A[a] = iv_fma(w, iv_recip_pos(V[a]), A[a]); break;
         }
     }
 }
@@ -388,7 +432,8 @@ static void ws_free(ws_t* w) {
 /* Enclosures of every output on subdomain k:
  *   Fc[o] : rigorous point value f_o(c) (interval sweep on [c,c])
  *   F[o]  : Mean Value Form f(c) + <G, X - c> (Definition 5), accumulated
- *           left to right over i; or NIE, or MVF intersected with NIE
+ *           left to right over i, each term G_i (X_i - c_i) added with one
+ *           rounding per end (iv_fma); or NIE, or MVF intersected with NIE
  *   G     : optional copy of the gradient enclosures [n_out][n]           */
 static void enclose_one(const tape_t* T, const double* box, const int32_t* splits, int64_t k,
                         const opts_t* o, ws_t* w, iv* F, iv* Fc, iv* Gout) {
@@ -407,7 +452,7 @@ static void enclose_one(const tape_t* T, const double* box, const int32_t* split
         iv mvf = w->Vc[out];
         for (int i = 0; i < n; ++i) {
             iv dx = {sub_dn(w->X[i].lo, w->c[i]), sub_up(w->X[i].hi, w->c[i])};
-            mvf = iv_add(mvf, iv_mul(G[i], dx));
+            mvf = iv_fma(G[i], dx, mvf);
         }
         const iv nie = w->V[out];
         iv r = mvf;
@@ -742,7 +787,8 @@ void orc_log_enclose(int64_t n, const double* x, int tight, double* lo, double* 
 }
 
 /* One interval operation on arrays of operands (for closed-form op tests):
- * opcode from the tape alphabet (100: reciprocal), x/y/r as [count][2]. */
+ * opcode from the tape alphabet (100: reciprocal, 105: fused r + x y with r
+ * the addend on entry), x/y/r as [count][2]. */
 void orc_iv_op(int opcode, int64_t count, const double* x, const double* y, int tight, double* r) {
     for (int64_t i = 0; i < count; ++i) {
         iv X = {x[2 * i], x[2 * i + 1]}, Y = {0, 0}, R;
@@ -758,6 +804,10 @@ void orc_iv_op(int opcode, int64_t count, const double* x, const double* y, int 
         case OP_LOG: R = iv_log(X, tight); break;
         case OP_NEG: R = iv_neg(X); break;
         case 100: R = iv_recip(X); break;   /* interval reciprocal */
+        case 105: {                         /* r + x y, fused: r holds the addend on entry */
+            iv Z = {r[2 * i], r[2 * i + 1]};
+            R = iv_fma(X, Y, Z);
+        } break;
         default: R = ENTIRE;
         }
         r[2 * i] = R.lo;

@@ -787,7 +787,8 @@ extern "C" ivb_status ivb_eval_op(int32_t opcode, int64_t n, const double* x, co
                                   void* cuda_stream) {
     if (n < 0 || !x || !r) return fail(nullptr, IVB_EINVAL, "ivb_eval_op: x and r are required");
     const bool binary = opcode == IVB_OP_ADD || opcode == IVB_OP_SUB || opcode == IVB_OP_MUL || opcode == IVB_OP_DIV ||
-                        opcode == IVB_EVAL_EMU_ADD || opcode == IVB_EVAL_EMU_SUB || opcode == IVB_EVAL_EMU_MUL;
+                        opcode == IVB_EVAL_EMU_ADD || opcode == IVB_EVAL_EMU_SUB || opcode == IVB_EVAL_EMU_MUL ||
+                        opcode == IVB_EVAL_FMA;
     const bool unary = opcode == IVB_OP_SQR || opcode == IVB_OP_SQRT || opcode == IVB_OP_EXP || opcode == IVB_OP_LOG ||
                        opcode == IVB_OP_NEG || opcode == IVB_EVAL_RECIP || opcode == IVB_EVAL_EMU_SQR;
     if (!binary && !unary) return fail(nullptr, IVB_EINVAL, "ivb_eval_op: unknown opcode");

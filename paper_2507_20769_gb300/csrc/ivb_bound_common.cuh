@@ -138,10 +138,10 @@ __device__ __forceinline__ void decode_dim(const char* rec, int n, int i, unsign
 
 // ------------------------------------------------------- Step 2 and the tests
 // one term of the Mean Value Form (Definition 5), summed left to right:
-// acc + G_i (X_i - c_i)
+// acc + G_i (X_i - c_i), product and sum fused (one directed rounding per end)
 __device__ __forceinline__ iv mvf_term(iv acc, iv Gi, iv Xi, double ci) {
     const iv dx = mk(sub_dn(Xi.lo, ci), sub_up(Xi.hi, ci));
-    return iv_add(acc, iv_mul(Gi, dx));
+    return iv_fma(Gi, dx, acc);
 }
 
 // enclosure of one output: MVF, NIE or their intersection; NaN -> ENTIRE

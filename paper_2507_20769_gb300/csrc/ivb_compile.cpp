@@ -275,12 +275,11 @@ std::string compile_tape(const ivb_tape* t, HostProgram& P, std::vector<Ins>& in
             value_cost(op, c);
             switch (op) {
             case OP_ADD: case OP_SUB: if (!az && !bz) c[ADD] += 2LL * n; break;
-            case OP_MUL: if (az || bz) c[MUL] += 2LL * n; else { c[MUL] += 4LL * n; c[ADD] += 2LL * n; } break;
+            case OP_MUL: c[MUL] += (az || bz) ? 2LL * n : 4LL * n; break;   // second product fused into the sum
             case OP_DIV:
                 c[RCP] += 2;
                 if (bz) c[MUL] += 2LL * n;
-                else if (az) c[MUL] += 4LL * n;
-                else { c[MUL] += 4LL * n; c[ADD] += 2LL * n; }
+                else c[MUL] += 4LL * n;                              // V * db fused into the difference
                 break;
             case OP_SQR: c[MUL] += 2 + 2LL * n; break;
             case OP_SQRT: c[MUL] += 2 + 2LL * n; c[RCP] += 2; break;
@@ -298,20 +297,21 @@ std::string compile_tape(const ivb_tape* t, HostProgram& P, std::vector<Ins>& in
             switch (op) {
             case OP_VAR: c[ADD] += 2; break;
             case OP_ADD: case OP_SUB: case OP_NEG: c[ADD] += acc; break;
-            case OP_MUL: c[MUL] += (an ? 0 : 2) + (bn ? 0 : 2); c[ADD] += acc; break;
-            case OP_DIV: c[RCP] += 2; c[MUL] += (an ? 0 : 2) + (bn ? 0 : 4); c[ADD] += acc; break;
-            case OP_SQR: c[MUL] += 4; c[ADD] += acc; break;
-            case OP_SQRT: c[MUL] += 4; c[RCP] += 2; c[ADD] += acc; break;
-            case OP_EXP: c[MUL] += 2; c[ADD] += acc; break;
-            case OP_LOG: c[RCP] += 2; c[MUL] += 2; c[ADD] += acc; break;
+            // product contributions: the accumulating add is fused into the multiply
+            case OP_MUL: c[MUL] += (an ? 0 : 2) + (bn ? 0 : 2); break;
+            case OP_DIV: c[RCP] += 2; c[MUL] += (an ? 0 : 2) + (bn ? 0 : 4); break;
+            case OP_SQR: c[MUL] += 4; break;
+            case OP_SQRT: c[MUL] += 4; c[RCP] += 2; break;
+            case OP_EXP: c[MUL] += 2; break;
+            case OP_LOG: c[RCP] += 2; c[MUL] += 2; break;
             }
         }
     };
     for (int64_t* c : {P.cnt_fwd, P.cnt_adj}) {
         c[RN] += 6LL * n;                                   // decode: endpoints and centre
         count_values(P.pt_begin, P.pt_count, c);            // point sweep f(c)
-        c[ADD] += 2LL * n + 2LL * n * no;                   // MVF: X - c once per dimension, the sum per output
-        c[MUL] += 2LL * n * no;
+        c[ADD] += 2LL * n;                                  // MVF: X - c once per dimension
+        c[MUL] += 2LL * n * no;                             // each term fused into the sum
     }
     count_tangents(P.tan_begin, P.tan_count, P.cnt_fwd);
     for (int o = 0; o < no; ++o) {

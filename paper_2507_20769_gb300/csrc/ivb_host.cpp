@@ -8,10 +8,13 @@
 // quotients and square roots (exact unless the result is within 2^-960 of
 // zero, where the result is widened by one step instead). exp and log are
 // the C library's (within one ulp) widened by two steps, as in the kernels.
-// Same value, tangent and adjoint rules as the kernels (Section 3.2):
-// ENTIRE on domain violations, 0 * inf = 0 in products.
+// The fused accumulation (acc + x*y with one rounding per end) switches the
+// rounding mode around one fma in a function of its own. Same value, tangent
+// and adjoint rules as the kernels (Section 3.2): ENTIRE on domain
+// violations, 0 * inf = 0 in products.
 #include "ivb_host.h"
 
+#include <cfenv>
 #include <cfloat>
 #include <cmath>
 #include <cstring>
@@ -94,6 +97,22 @@ double log_dir(double x, bool up) {
     return widen(std::log(x), up);
 }
 
+// a b + c rounded once toward -inf (up = false) or +inf: the rounding mode is
+// switched around one fma; volatile operands and result keep the arithmetic
+// between the two switches
+__attribute__((noinline, optimize("rounding-math"))) double fma_dir(double a, double b, double c, bool up) {
+    volatile double va = a, vb = b, vc = c, r;
+    const int mode = std::fegetround();
+    std::fesetround(up ? FE_UPWARD : FE_DOWNWARD);
+    r = std::fma(va, vb, vc);
+    std::fesetround(mode);
+    return r;
+}
+// c + a b with one rounding, a zero factor adding an exact zero
+double fprod_dir(double a, double b, double c, bool up) {
+    return (a == 0.0 || b == 0.0) ? add_dir(c, 0.0, up) : fma_dir(a, b, c, up);
+}
+
 inline hiv mk(double lo, double hi) { return hiv{lo, hi}; }
 inline hiv entire() { return mk(-INF, INF); }
 inline hiv zero() { return mk(0.0, 0.0); }
@@ -108,6 +127,16 @@ hiv iv_mul(hiv x, hiv y) {
                          mul_dir(x.hi, y.hi, false)};
     const double q[4] = {mul_dir(x.lo, y.lo, true), mul_dir(x.lo, y.hi, true), mul_dir(x.hi, y.lo, true),
                          mul_dir(x.hi, y.hi, true)};
+    return mk(std::fmin(std::fmin(p[0], p[1]), std::fmin(p[2], p[3])),
+              std::fmax(std::fmax(q[0], q[1]), std::fmax(q[2], q[3])));
+}
+// acc + x*y with one directed rounding per end: the extreme of the four
+// fused candidates (fmin / fmax skip NaN, as the kernels' pair selection does)
+hiv iv_fma(hiv x, hiv y, hiv acc) {
+    const double p[4] = {fprod_dir(x.lo, y.lo, acc.lo, false), fprod_dir(x.lo, y.hi, acc.lo, false),
+                         fprod_dir(x.hi, y.lo, acc.lo, false), fprod_dir(x.hi, y.hi, acc.lo, false)};
+    const double q[4] = {fprod_dir(x.lo, y.lo, acc.hi, true), fprod_dir(x.lo, y.hi, acc.hi, true),
+                         fprod_dir(x.hi, y.lo, acc.hi, true), fprod_dir(x.hi, y.hi, acc.hi, true)};
     return mk(std::fmin(std::fmin(p[0], p[1]), std::fmin(p[2], p[3])),
               std::fmax(std::fmax(q[0], q[1]), std::fmax(q[2], q[3])));
 }
@@ -220,8 +249,8 @@ void host_gradient(const HostTape& H, const double* box, int o, int grad_mode, h
                 case OP_ADD: Dt[d] = iv_add(Da[d], Db[d]); break;
                 case OP_SUB: Dt[d] = iv_sub(Da[d], Db[d]); break;
                 case OP_NEG: Dt[d] = iv_neg(Da[d]); break;
-                case OP_MUL: Dt[d] = iv_add(iv_mul(Da[d], B), iv_mul(A, Db[d])); break;
-                case OP_DIV: Dt[d] = iv_mul(iv_sub(Da[d], iv_mul(V[t], Db[d])), iv_recip(B)); break;
+                case OP_MUL: Dt[d] = iv_fma(A, Db[d], iv_mul(Da[d], B)); break;
+                case OP_DIV: Dt[d] = iv_mul(iv_fma(iv_neg(V[t]), Db[d], Da[d]), iv_recip(B)); break;
                 case OP_SQR: Dt[d] = iv_mul(iv_twice(A), Da[d]); break;
                 case OP_SQRT: Dt[d] = iv_mul(Da[d], iv_recip_pos(iv_twice(V[t]))); break;
                 case OP_EXP: Dt[d] = iv_mul(V[t], Da[d]); break;
@@ -245,18 +274,18 @@ void host_gradient(const HostTape& H, const double* box, int o, int grad_mode, h
         case OP_SUB: W[e.a] = iv_add(W[e.a], w); W[e.b] = iv_sub(W[e.b], w); break;
         case OP_NEG: W[e.a] = iv_sub(W[e.a], w); break;
         case OP_MUL:
-            W[e.a] = iv_add(W[e.a], iv_mul(w, V[e.b]));
-            W[e.b] = iv_add(W[e.b], iv_mul(w, V[e.a]));
+            W[e.a] = iv_fma(w, V[e.b], W[e.a]);
+            W[e.b] = iv_fma(w, V[e.a], W[e.b]);
             break;
         case OP_DIV: {
             const hiv R = iv_recip(V[e.b]);
-            W[e.a] = iv_add(W[e.a], iv_mul(w, R));
-            W[e.b] = iv_sub(W[e.b], iv_mul(iv_mul(w, V[t]), R));
+            W[e.a] = iv_fma(w, R, W[e.a]);
+            W[e.b] = iv_fma(iv_neg(iv_mul(w, V[t])), R, W[e.b]);
         } break;
-        case OP_SQR: W[e.a] = iv_add(W[e.a], iv_mul(w, iv_twice(V[e.a]))); break;
-        case OP_SQRT: W[e.a] = iv_add(W[e.a], iv_mul(w, iv_recip_pos(iv_twice(V[t])))); break;
-        case OP_EXP: W[e.a] = iv_add(W[e.a], iv_mul(w, V[t])); break;
-        case OP_LOG: W[e.a] = iv_add(W[e.a], iv_mul(w, iv_recip_pos(V[e.a]))); break;
+        case OP_SQR: W[e.a] = iv_fma(w, iv_twice(V[e.a]), W[e.a]); break;
+        case OP_SQRT: W[e.a] = iv_fma(w, iv_recip_pos(iv_twice(V[t])), W[e.a]); break;
+        case OP_EXP: W[e.a] = iv_fma(w, V[t], W[e.a]); break;
+        case OP_LOG: W[e.a] = iv_fma(w, iv_recip_pos(V[e.a]), W[e.a]); break;
         }
     }
 }

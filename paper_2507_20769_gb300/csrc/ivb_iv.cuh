@@ -163,28 +163,65 @@ __device__ __forceinline__ iv iv_neg(iv x) { return mk(ineg(x.hi), ineg(x.lo)); 
 // the same two directed multiplies; lanes where both factors straddle 0 need a
 // second pair, issued only when some lane of the warp needs it (warp-uniform
 // branch: no FP64 instruction runs with idle lanes for the common case).
-template <int E> __device__ __forceinline__ iv iv_mul_t(iv x, iv y) {
+struct MulPairs {
+    double lx, ly, ux, uy;   // factors of the lower and of the upper end
+    bool mm;                 // both straddle 0: second pair x.hi*y.lo | x.hi*y.hi
+};
+__device__ __forceinline__ MulPairs mul_pairs(iv x, iv y) {
     const bool xP = ge0(x.lo), xN = !xP && le0(x.hi), xM = !xP && !xN;
     const bool yP = ge0(y.lo), yN = !yP && le0(y.hi), yM = !yP && !yN;
-    const bool mm = xM && yM;
+    MulPairs q;
+    q.mm = xM && yM;
     // endpoint pairs (lower | upper):
     //   P,P: lo*lo | hi*hi   P,M: hi*lo | hi*hi   P,N: hi*lo | lo*hi
     //   M,P: lo*hi | hi*hi   M,N: hi*lo | lo*lo   M,M: lo*hi, hi*lo | lo*lo, hi*hi
     //   N,P: lo*hi | hi*lo   N,M: lo*hi | lo*lo   N,N: hi*hi | lo*lo
-    const double lx = mm ? x.lo : ((xP ? !yP : yN) ? x.hi : x.lo);
-    const double ly = mm ? y.hi : ((xP || (xM && yN)) ? y.lo : y.hi);
-    const double ux = mm ? x.lo : ((xP ? !yN : yP) ? x.hi : x.lo);
-    const double uy = mm ? y.lo : ((xP || (xM && yP)) ? y.hi : y.lo);
-    double lo = prod_dn_t<E>(lx, ly), hi = prod_up_t<E>(ux, uy);
-    if (__any_sync(__activemask(), mm)) {
-        const double lo2 = prod_dn_t<E>(mm ? x.hi : lx, mm ? y.lo : ly);
-        const double hi2 = prod_up_t<E>(mm ? x.hi : ux, mm ? y.hi : uy);
+    q.lx = q.mm ? x.lo : ((xP ? !yP : yN) ? x.hi : x.lo);
+    q.ly = q.mm ? y.hi : ((xP || (xM && yN)) ? y.lo : y.hi);
+    q.ux = q.mm ? x.lo : ((xP ? !yN : yP) ? x.hi : x.lo);
+    q.uy = q.mm ? y.lo : ((xP || (xM && yP)) ? y.hi : y.lo);
+    return q;
+}
+template <int E> __device__ __forceinline__ iv iv_mul_t(iv x, iv y) {
+    const MulPairs q = mul_pairs(x, y);
+    double lo = prod_dn_t<E>(q.lx, q.ly), hi = prod_up_t<E>(q.ux, q.uy);
+    if (__any_sync(__activemask(), q.mm)) {
+        const double lo2 = prod_dn_t<E>(q.mm ? x.hi : q.lx, q.mm ? y.lo : q.ly);
+        const double hi2 = prod_up_t<E>(q.mm ? x.hi : q.ux, q.mm ? y.hi : q.uy);
         lo = imin(lo, lo2);
         hi = imax(hi, hi2);
     }
     return mk(lo, hi);
 }
 __device__ __forceinline__ iv iv_mul(iv x, iv y) { return iv_mul_t<IVB_EMU>(x, y); }
+
+// acc + x*y with one directed rounding per end (fused multiply-add): each end
+// adds the extreme endpoint product to the accumulator's end in one rounding,
+// RD(acc.lo + min) and RU(acc.hi + max). Same pair selection as the product;
+// a zero factor gives an exact zero product (0 * inf = 0), i.e. RD(acc.lo + 0)
+// = acc.lo and RU(acc.hi + 0) = acc.hi with -0 turned into +0. One FP64 fma per
+// end instead of a multiply and an add. Never emulated (the emulation policy
+// covers stand-alone adds and multiplies only), so every policy gives the same
+// bits.
+__device__ __forceinline__ double fprod_dn(double x, double y, double c) {
+    const double p = __fma_rd(x, y, c);
+    return (is0(x) || is0(y)) ? c : p;
+}
+__device__ __forceinline__ double fprod_up(double x, double y, double c) {
+    const double p = __fma_ru(x, y, c);
+    return (is0(x) || is0(y)) ? (is0(c) ? 0.0 : c) : p;
+}
+__device__ __forceinline__ iv iv_fma(iv x, iv y, iv acc) {
+    const MulPairs q = mul_pairs(x, y);
+    double lo = fprod_dn(q.lx, q.ly, acc.lo), hi = fprod_up(q.ux, q.uy, acc.hi);
+    if (__any_sync(__activemask(), q.mm)) {
+        const double lo2 = fprod_dn(q.mm ? x.hi : q.lx, q.mm ? y.lo : q.ly, acc.lo);
+        const double hi2 = fprod_up(q.mm ? x.hi : q.ux, q.mm ? y.hi : q.uy, acc.hi);
+        lo = imin(lo, lo2);
+        hi = imax(hi, hi2);
+    }
+    return mk(lo, hi);
+}
 
 // 2*x rounded toward -inf / +inf: exact (an exponent increment on the integer
 // pipe, or a shift for zero and subnormals) unless |x| >= 2^1023, where the

@@ -12,7 +12,7 @@
 //
 // Every statement calls the same interval primitive on the same operands as
 // the interpreter does, in the same order wherever the order changes a
-// rounded result (adjoint accumulation, the MVF sum), so the bounds are
+// rounded result (fused adjoint accumulation, the MVF sum), so the bounds are
 // bit-identical to the interpreter's. What changes: no instruction stream,
 // operands in registers, and the compiler is free to interleave independent
 // operations, which hides the latency of the narrow FP64 pipe.
@@ -147,7 +147,7 @@ struct Gen {
                     std::string t;
                     if (az) t = "iv_mul(A, " + tan(bk, bi, d) + ")";
                     else if (bz) t = "iv_mul(" + tan(ak, ai, d) + ", B)";
-                    else t = "iv_add(iv_mul(" + tan(ak, ai, d) + ", B), iv_mul(A, " + tan(bk, bi, d) + "))";
+                    else t = "iv_fma(A, " + tan(bk, bi, d) + ", iv_mul(" + tan(ak, ai, d) + ", B))";
                     line(j, T + S(d) + " = " + t + ";");
                 }
                 break;
@@ -157,7 +157,7 @@ struct Gen {
                     std::string t;
                     if (bz) t = "iv_mul(" + tan(ak, ai, d) + ", R)";
                     else if (az) t = "iv_mul(iv_neg(iv_mul(V, " + tan(bk, bi, d) + ")), R)";
-                    else t = "iv_mul(iv_sub(" + tan(ak, ai, d) + ", iv_mul(V, " + tan(bk, bi, d) + ")), R)";
+                    else t = "iv_mul(iv_fma(iv_neg(V), " + tan(bk, bi, d) + ", " + tan(ak, ai, d) + "), R)";
                     line(j, T + S(d) + " = " + t + ";");
                 }
                 break;
@@ -199,43 +199,50 @@ struct Gen {
             const uint32_t Ak = (R.w3 >> 16) & 3u, Bk = (R.w3 >> 18) & 3u;
             const std::string Av = val('r', Ak, R.w2 & 0xFFFFu), Bv = val('r', Bk, R.w2 >> 16);
             const std::string V = "r" + S(R.w3 & 0xFFFFu);
-            std::string ca, cb;
-            bool sub_a = false, sub_b = false;
+            // contribution to operand a: ax * ay (a_prod) or +-W; to operand b likewise
+            std::string ax = "W", ay, bx = "W", by;
+            bool a_prod = true, b_prod = true, sub_a = false, sub_b = false;
             line(ind, "{");
             const int j = ind + 1;
             line(j, "const iv W = " + W + ";");
             switch (op) {
-            case OP_ADD: ca = "W"; cb = "W"; break;
-            case OP_SUB: ca = "W"; cb = "W"; sub_b = true; break;
-            case OP_NEG: ca = "W"; sub_a = true; break;
-            case OP_MUL:
-                if (!a_none) ca = "iv_mul(W, " + Bv + ")";
-                if (!b_none) cb = "iv_mul(W, " + Av + ")";
-                break;
+            case OP_ADD: a_prod = b_prod = false; break;
+            case OP_SUB: a_prod = b_prod = false; sub_b = true; break;
+            case OP_NEG: a_prod = false; sub_a = true; break;
+            case OP_MUL: ay = Bv; by = Av; break;
             case OP_DIV:
                 line(j, "const iv Rb = iv_recip(" + Bv + ");");
-                if (!a_none) ca = "iv_mul(W, Rb)";
-                if (!b_none) cb = "iv_mul(iv_mul(W, " + V + "), Rb)";
-                sub_b = true;
+                ay = "Rb";
+                if (!b_none) {
+                    line(j, "const iv nb = iv_neg(iv_mul(W, " + V + "));");   // b gets -(W V) / B
+                    bx = "nb";
+                }
+                by = "Rb";
                 break;
-            case OP_SQR: ca = "iv_mul(W, iv_twice(" + Av + "))"; break;
-            case OP_SQRT: ca = "iv_mul(W, iv_recip_pos(iv_twice(" + V + ")))"; break;
-            case OP_EXP: ca = "iv_mul(W, " + V + ")"; break;
-            case OP_LOG: ca = "iv_mul(W, iv_recip_pos(" + Av + "))"; break;
-            default: ca = "entire()"; cb = "entire()";
+            case OP_SQR: ay = "iv_twice(" + Av + ")"; break;
+            case OP_SQRT: ay = "iv_recip_pos(iv_twice(" + V + "))"; break;
+            case OP_EXP: ay = V; break;
+            case OP_LOG: ay = "iv_recip_pos(" + Av + ")"; break;
+            default: a_prod = b_prod = false; ax = bx = "entire()";
             }
-            // both contributions are formed before either slot is written
-            if (!a_none) line(j, "const iv ca = " + ca + ";");
-            if (!b_none) line(j, "const iv cb = " + cb + ";");
+            // the factors are formed before either slot is written
+            if (!a_none && a_prod) line(j, "const iv ya = " + ay + ";");
+            if (!b_none && b_prod) line(j, "const iv yb = " + by + ";");
             if (!a_none) {
                 const std::string u = "w" + S(R.w1 & 0xFFFFu);
-                line(j, u + " = " + (a_init ? (sub_a ? "iv_neg(ca)" : "ca")
-                                            : (sub_a ? "iv_sub(" + u + ", ca)" : "iv_add(" + u + ", ca)")) + ";");
+                std::string v;
+                if (a_prod) v = a_init ? "iv_mul(" + ax + ", ya)" : "iv_fma(" + ax + ", ya, " + u + ")";
+                else if (a_init) v = sub_a ? "iv_neg(" + ax + ")" : ax;
+                else v = sub_a ? "iv_sub(" + u + ", " + ax + ")" : "iv_add(" + u + ", " + ax + ")";
+                line(j, u + " = " + v + ";");
             }
             if (!b_none) {
                 const std::string u = "w" + S(R.w1 >> 16);
-                line(j, u + " = " + (b_init ? (sub_b ? "iv_neg(cb)" : "cb")
-                                            : (sub_b ? "iv_sub(" + u + ", cb)" : "iv_add(" + u + ", cb)")) + ";");
+                std::string v;
+                if (b_prod) v = b_init ? "iv_mul(" + bx + ", yb)" : "iv_fma(" + bx + ", yb, " + u + ")";
+                else if (b_init) v = sub_b ? "iv_neg(" + bx + ")" : bx;
+                else v = sub_b ? "iv_sub(" + u + ", " + bx + ")" : "iv_add(" + u + ", " + bx + ")";
+                line(j, u + " = " + v + ";");
             }
             line(ind, "}");
         }

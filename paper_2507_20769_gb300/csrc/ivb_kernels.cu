@@ -120,7 +120,7 @@ __device__ void run_tangents(const Ins* __restrict__ ins, int count, const Sweep
                 iv t;
                 if (az) t = iv_mul(A, load_tan(C, bk, bi, base, rec, d));
                 else if (bz) t = iv_mul(load_tan(C, ak, ai, base, rec, d), B);
-                else t = iv_add(iv_mul(load_tan(C, ak, ai, base, rec, d), B), iv_mul(A, load_tan(C, bk, bi, base, rec, d)));
+                else t = iv_fma(A, load_tan(C, bk, bi, base, rec, d), iv_mul(load_tan(C, ak, ai, base, rec, d), B));
                 C.F.put(o + 2 + 2 * d, t);
             }
             break;
@@ -130,7 +130,7 @@ __device__ void run_tangents(const Ins* __restrict__ ins, int count, const Sweep
                 iv t;
                 if (bz) t = iv_mul(load_tan(C, ak, ai, base, rec, d), R);
                 else if (az) t = iv_mul(iv_neg(iv_mul(V, load_tan(C, bk, bi, base, rec, d))), R);
-                else t = iv_mul(iv_sub(load_tan(C, ak, ai, base, rec, d), iv_mul(V, load_tan(C, bk, bi, base, rec, d))), R);
+                else t = iv_mul(iv_fma(iv_neg(V), load_tan(C, bk, bi, base, rec, d), load_tan(C, ak, ai, base, rec, d)), R);
                 C.F.put(o + 2 + 2 * d, t);
             }
         } break;
@@ -156,7 +156,9 @@ __device__ void run_tangents(const Ins* __restrict__ ins, int count, const Sweep
 
 // reverse sweep of one output (reverse-mode interval AD): adjoint slots at
 // `abase` (2 units each), forward values in tape records at `tbase`, gradient
-// accumulators at `gbase`. Operand a is updated before operand b.
+// accumulators at `gbase`. Operand a is updated before operand b. A product
+// contribution x*y to a slot already written is accumulated with one directed
+// rounding per end (iv_fma); the first write stores the product.
 __device__ void run_reverse(const RIns* __restrict__ rins, int count, const SweepCtx& C, int abase, int tbase,
                             int gbase) {
     for (int i = 0; i < count; ++i) {
@@ -171,56 +173,44 @@ __device__ void run_reverse(const RIns* __restrict__ rins, int count, const Swee
         const bool a_init = (R.w0 >> 5) & 1u, b_init = (R.w0 >> 6) & 1u;
         const bool a_none = (R.w0 >> 7) & 1u, b_none = (R.w0 >> 8) & 1u;
         const uint32_t Ak = (R.w3 >> 16) & 3u, Bk = (R.w3 >> 18) & 3u;
-        iv ca, cb;
-        bool sub_b = false, sub_a = false;
+        // contribution to operand a: ax * ay (a_prod) or +-W; to operand b likewise
+        iv ax = W, ay = W, bx = W, by = W;
+        bool a_prod = true, b_prod = true, sub_b = false, sub_a = false;
         switch (op) {
-        case OP_ADD: ca = W; cb = W; break;
-        case OP_SUB: ca = W; cb = W; sub_b = true; break;
-        case OP_NEG: ca = W; sub_a = true; break;
+        case OP_ADD: a_prod = b_prod = false; break;
+        case OP_SUB: a_prod = b_prod = false; sub_b = true; break;
+        case OP_NEG: a_prod = false; sub_a = true; break;
         case OP_MUL: {
-            const iv A = load_val(C, Ak, R.w2 & 0xFFFFu, tbase, 2);
-            const iv B = load_val(C, Bk, R.w2 >> 16, tbase, 2);
-            if (!a_none) ca = iv_mul(W, B);
-            if (!b_none) cb = iv_mul(W, A);
+            ay = load_val(C, Bk, R.w2 >> 16, tbase, 2);
+            by = load_val(C, Ak, R.w2 & 0xFFFFu, tbase, 2);
         } break;
         case OP_DIV: {
             const iv B = load_val(C, Bk, R.w2 >> 16, tbase, 2);
             const iv V = C.F.get(tbase + 2 * (int)(R.w3 & 0xFFFFu));
-            const iv Rb = iv_recip(B);
-            if (!a_none) ca = iv_mul(W, Rb);
-            if (!b_none) cb = iv_mul(iv_mul(W, V), Rb);
-            sub_b = true;
+            ay = iv_recip(B);
+            bx = iv_neg(iv_mul(W, V));            // b gets -(W V) / B
+            by = ay;
         } break;
-        case OP_SQR: {
-            const iv A = load_val(C, Ak, R.w2 & 0xFFFFu, tbase, 2);
-            ca = iv_mul(W, iv_twice(A));
-        } break;
-        case OP_SQRT: {
-            const iv V = C.F.get(tbase + 2 * (int)(R.w3 & 0xFFFFu));
-            ca = iv_mul(W, iv_recip_pos(iv_twice(V)));
-        } break;
-        case OP_EXP: {
-            const iv V = C.F.get(tbase + 2 * (int)(R.w3 & 0xFFFFu));
-            ca = iv_mul(W, V);
-        } break;
-        case OP_LOG: {
-            const iv A = load_val(C, Ak, R.w2 & 0xFFFFu, tbase, 2);
-            ca = iv_mul(W, iv_recip_pos(A));
-        } break;
-        default: ca = entire(); cb = entire();
+        case OP_SQR: ay = iv_twice(load_val(C, Ak, R.w2 & 0xFFFFu, tbase, 2)); break;
+        case OP_SQRT: ay = iv_recip_pos(iv_twice(C.F.get(tbase + 2 * (int)(R.w3 & 0xFFFFu)))); break;
+        case OP_EXP: ay = C.F.get(tbase + 2 * (int)(R.w3 & 0xFFFFu)); break;
+        case OP_LOG: ay = iv_recip_pos(load_val(C, Ak, R.w2 & 0xFFFFu, tbase, 2)); break;
+        default: a_prod = b_prod = false; ax = bx = entire();
         }
         if (!a_none) {
             const int u = abase + 2 * (int)(R.w1 & 0xFFFFu);
             iv v;
-            if (a_init) v = sub_a ? iv_neg(ca) : ca;
-            else v = sub_a ? iv_sub(C.F.get(u), ca) : iv_add(C.F.get(u), ca);
+            if (a_prod) v = a_init ? iv_mul(ax, ay) : iv_fma(ax, ay, C.F.get(u));
+            else if (a_init) v = sub_a ? iv_neg(ax) : ax;
+            else v = sub_a ? iv_sub(C.F.get(u), ax) : iv_add(C.F.get(u), ax);
             C.F.put(u, v);
         }
         if (!b_none) {
             const int u = abase + 2 * (int)(R.w1 >> 16);
             iv v;
-            if (b_init) v = sub_b ? iv_neg(cb) : cb;
-            else v = sub_b ? iv_sub(C.F.get(u), cb) : iv_add(C.F.get(u), cb);
+            if (b_prod) v = b_init ? iv_mul(bx, by) : iv_fma(bx, by, C.F.get(u));
+            else if (b_init) v = sub_b ? iv_neg(bx) : bx;
+            else v = sub_b ? iv_sub(C.F.get(u), bx) : iv_add(C.F.get(u), bx);
             C.F.put(u, v);
         }
     }
@@ -513,7 +503,7 @@ __global__ void k_eval_op(int opcode, long long n, const double* __restrict__ x,
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const iv X = mk(x[2 * i], x[2 * i + 1]);
         const iv Y = y ? mk(y[2 * i], y[2 * i + 1]) : X;
-        const iv R = eval_hook(opcode, X, Y);
+        const iv R = opcode == 105 ? iv_fma(X, Y, mk(r[2 * i], r[2 * i + 1])) : eval_hook(opcode, X, Y);
         r[2 * i] = R.lo;
         r[2 * i + 1] = R.hi;
     }

@@ -199,17 +199,24 @@ def ivb_fp64_probe(which: str, iters: int = 1024) -> float:
 
 IVB_EVAL_RECIP = 100
 IVB_EVAL_EMU_ADD, IVB_EVAL_EMU_SUB, IVB_EVAL_EMU_MUL, IVB_EVAL_EMU_SQR = 101, 102, 103, 104
+IVB_EVAL_FMA = 105
 
 
-def ivb_eval_op(opcode: int, x, y=None):
+def ivb_eval_op(opcode: int, x, y=None, acc=None):
     """test hook: one interval operation of the kernels' arithmetic on CUDA
-    tensors of intervals [n, 2]; returns a new [n, 2] tensor"""
+    tensors of intervals [n, 2]; returns a new [n, 2] tensor (IVB_EVAL_FMA:
+    acc + x*y, acc required)"""
     import torch
     if not (_is_torch(x) and x.is_cuda):
         raise TypeError("ivb_eval_op takes CUDA tensors")
     x = x.contiguous()
     y = None if y is None else y.contiguous()
-    r = torch.empty_like(x)
+    if opcode == IVB_EVAL_FMA:
+        if acc is None:
+            raise ValueError("IVB_EVAL_FMA needs the addend acc")
+        r = acc.contiguous().clone()
+    else:
+        r = torch.empty_like(x)
     _check(lib().ivb_eval_op(int(opcode), int(x.shape[0]), _ptr(x), _ptr(y), _ptr(r), _stream_for(x)))
     return r
 

@@ -128,6 +128,42 @@ def test_unary_ops_bit_exact(opcode):
     assert not bad.any(), (X[bad][:3], R[bad][:3], Ro[bad][:3])
 
 
+def test_fused_accumulation_bit_exact():
+    """acc + x*y with one directed rounding per end (IVB_EVAL_FMA, the adjoint,
+    tangent and Mean Value Form accumulation) equals the oracle's: every sign
+    case of x and y, zero endpoints, points, wide exponent ranges, infinite
+    factor ends and special operands"""
+    rng = np.random.default_rng(105)
+    n = 200000
+    X = intervals(rng, n, -300, 300)
+    Y = intervals(rng, n, -300, 300)
+    Z = intervals(rng, n, -300, 300)
+    m = min(len(X), len(Y), len(Z))
+    X, Y, Z = X[:m], Y[:m], Z[:m]
+    X[::11, 0] = 0.0                                         # zero lower ends ...
+    X[::11, 1] = np.abs(X[::11, 1])                          # ... of valid intervals
+    Y[5::13, 1] = 0.0
+    Y[5::13, 0] = np.minimum(Y[5::13, 0], 0.0)
+    Z[3::17] = -Z[3::17, ::-1]                               # addends of both signs
+    x = torch.from_numpy(np.ascontiguousarray(X)).to(DEV)
+    y = torch.from_numpy(np.ascontiguousarray(Y)).to(DEV)
+    z = torch.from_numpy(np.ascontiguousarray(Z)).to(DEV)
+    R = ivb.ivb_eval_op(ivb.IVB_EVAL_FMA, x, y, acc=z).cpu().numpy()
+    Ro = oracle.iv_fma(X, Y, Z)
+    bad = ~((R == Ro) | (np.isnan(R) & np.isnan(Ro))).all(axis=1)
+    assert not bad.any(), (X[bad][:3], Y[bad][:3], Z[bad][:3], R[bad][:3], Ro[bad][:3])
+    # infinite factor ends with finite addends
+    F = np.array([[-np.inf, 1.0], [0.0, np.inf], [-2.0, np.inf], [-np.inf, np.inf], [1.0, 1.0], [0.0, 0.0]])
+    A = np.array([[-1.0, 2.0], [0.5, 0.75], [-0.0, 0.0]])
+    Xs = np.repeat(F, len(F) * len(A), axis=0)
+    Ys = np.tile(np.repeat(F, len(A), axis=0), (len(F), 1))
+    Zs = np.tile(A, (len(F) * len(F), 1))
+    R = ivb.ivb_eval_op(ivb.IVB_EVAL_FMA, torch.from_numpy(Xs).to(DEV), torch.from_numpy(Ys).to(DEV),
+                        acc=torch.from_numpy(Zs).to(DEV)).cpu().numpy()
+    Ro = oracle.iv_fma(Xs, Ys, Zs)
+    assert (((R == Ro) | (np.isnan(R) & np.isnan(Ro))).all(axis=1)).all()
+
+
 def ulps(a, b):
     ia = np.asarray(a, np.float64).view(np.int64)
     ib = np.asarray(b, np.float64).view(np.int64)

@@ -155,6 +155,44 @@ def test_binary_ops_exact_rational(opcode):
         _check_tight(rl, rh, *ex)
 
 
+def test_fused_accumulation_exact_rational():
+    """acc + x*y with one directed rounding per end (the adjoint accumulation,
+    tangent rules and Mean Value Form sum): on random operands of every sign
+    case the ends are the tightest doubles around acc.lo + min and acc.hi + max
+    of the exact endpoint products -- which a rounding after the product
+    (unfused) misses on part of these operands"""
+    rng = np.random.default_rng(105)
+    X = rng.uniform(-5, 5, (600, 2)); X.sort(1)
+    Y = rng.uniform(-5, 5, (600, 2)); Y.sort(1)
+    Z = rng.uniform(-50, 50, (600, 2)); Z.sort(1)
+    X[::3] = np.abs(X[::3]); X[::3].sort(1)
+    Y[1::3] = -np.abs(Y[1::3]); Y[1::3].sort(1)
+    X[2::7, 0] = 0.0                                   # zero endpoints
+    R = oracle.iv_fma(X, Y, Z)
+    unfused = oracle.iv_op(W.OP_ADD, Z, oracle.iv_op(W.OP_MUL, X, Y))
+    differs = 0
+    for (xl, xh), (yl, yh), (zl, zh), (rl, rh), u in zip(X, Y, Z, R, unfused):
+        P = [Fraction(p) * Fraction(q) for p in (xl, xh) for q in (yl, yh)]
+        _check_tight(rl, rh, Fraction(zl) + min(P), Fraction(zh) + max(P))
+        differs += (rl, rh) != tuple(u)
+    assert differs > 20
+
+
+def test_fused_accumulation_special_cases():
+    """zero factors add an exact zero (0 * inf = 0), -0 + 0 rounds up to +0,
+    infinite products, and an addend of zero gives the directed product"""
+    fma = lambda x, y, z: oracle.iv_fma([x], [y], [z])[0].tolist()
+    assert fma([0.0, 0.0], [-INF, INF], [1.0, 2.0]) == [1.0, 2.0]
+    r = fma([0.0, 0.0], [3.0, 4.0], [-0.0, -0.0])
+    assert r == [0.0, 0.0] and np.signbit(r[0]) and not np.signbit(r[1])
+    assert fma([1.0, INF], [1.0, 2.0], [0.0, 1.0]) == [1.0, INF]
+    assert fma([-1.0, 1.0], [-INF, INF], [0.0, 0.0]) == [-INF, INF]
+    third = oracle.iv_op(W.OP_DIV, [[1.0, 1.0]], [[3.0, 3.0]])[0].tolist()
+    assert fma([1.0, 1.0], third, [0.0, 0.0]) == third
+    p = oracle.iv_op(W.OP_MUL, [[0.1, 0.3]], [[-0.7, 0.9]])[0].tolist()
+    assert fma([0.1, 0.3], [-0.7, 0.9], [0.0, 0.0]) == p
+
+
 def test_textbook_values():
     """Exact textbook results on representable operands."""
     iv = lambda op, x, y=None: oracle.iv_op(op, [x], None if y is None else [y])[0].tolist()

@@ -32,14 +32,23 @@ MUTANTS = [
      "case OP_SUB: A[a] = iv_add(A[a], w); A[b] = iv_sub(A[b], w); break;",
      "case OP_SUB: A[a] = iv_add(A[a], w); A[b] = iv_add(A[b], w); break;"),
     ("adjoint of a product uses the wrong operand",
-     "            A[a] = iv_add(A[a], iv_mul(w, V[b]));",
-     "            A[a] = iv_add(A[a], iv_mul(w, V[a]));"),
+     "            A[a] = iv_fma(w, V[b], A[a]);",
+     "            A[a] = iv_fma(w, V[a], A[a]);"),
     ("tangent of a product drops a term",
-     "for (int d = 0; d < n; ++d) Dt[d] = iv_add(iv_mul(Da[d], V[b]), iv_mul(V[a], Db[d]));",
+     "for (int d = 0; d < n; ++d) Dt[d] = iv_fma(V[a], Db[d], iv_mul(Da[d], V[b]));",
      "for (int d = 0; d < n; ++d) Dt[d] = iv_mul(Da[d], V[b]);"),
     ("tangent of a quotient transposes an operand",
-     "for (int d = 0; d < n; ++d) Dt[d] = iv_mul(iv_sub(Da[d], iv_mul(V[t], Db[d])), R);",
-     "for (int d = 0; d < n; ++d) Dt[d] = iv_mul(iv_sub(Da[d], iv_mul(V[t], Da[d])), R);"),
+     "for (int d = 0; d < n; ++d) Dt[d] = iv_mul(iv_fma(iv_neg(V[t]), Db[d], Da[d]), R);",
+     "for (int d = 0; d < n; ++d) Dt[d] = iv_mul(iv_fma(iv_neg(V[t]), Da[d], Da[d]), R);"),
+    ("fused accumulation rounds its lower end upward",
+     "static double fprod_dn(double x, double y, double z) { return (x == 0.0 || y == 0.0) ? add_dn(z, 0.0) : fma_dn(x, y, z); }",
+     "static double fprod_dn(double x, double y, double z) { return (x == 0.0 || y == 0.0) ? add_dn(z, 0.0) : fma_up(x, y, z); }"),
+    ("fused accumulation drops an endpoint product",
+     "    r.lo = minnn(minnn(fprod_dn(x.lo, y.lo, acc.lo), fprod_dn(x.lo, y.hi, acc.lo)),",
+     "    r.lo = minnn(minnn(fprod_dn(x.lo, y.lo, acc.lo), fprod_dn(x.lo, y.lo, acc.lo)),"),
+    ("adjoint of a quotient keeps the sign of its second operand",
+     "            A[b] = iv_fma(iv_neg(iv_mul(w, V[t])), R, A[b]);",
+     "            A[b] = iv_fma(iv_mul(w, V[t]), R, A[b]);"),
     ("square drops the factor two in its derivative",
      "            R = iv_twice(V[a]);\n            for (int d = 0; d < n; ++d) Dt[d] = iv_mul(R, Da[d]);",
      "            R = V[a];\n            for (int d = 0; d < n; ++d) Dt[d] = iv_mul(R, Da[d]);"),
