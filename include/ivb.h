@@ -289,6 +289,15 @@ ivb_status ivb_bnb_solve(ivb_problem* p, int32_t n, const double* root, const iv
 ivb_status ivb_propagate(const ivb_tape* tape, int32_t n_boxes, const double* boxes, double ub,
                          int32_t passes, double* boxes_out, uint8_t* infeasible);
 
+/* Enclosure of the gradient of output `output` (index into the tape's
+ * outputs) over one box [n_vars][2], on the host, no GPU needed: the kernels'
+ * tangent (grad_mode IVB_GRAD_FORWARD) or reverse adjoint rules (Section 3.2),
+ * fused accumulation included, outward-rounded on the CPU. G receives
+ * [n_vars][2]. This is what the B&B's descent corner reads. IVB_EINVAL for a
+ * bad output index or grad_mode, IVB_ETAPE for an invalid tape. */
+ivb_status ivb_host_gradient(const ivb_tape* tape, const double* box, int32_t output, int32_t grad_mode,
+                             double* G);
+
 /* Tuning actually used by the batched path after autotuning (may be NULL):
  * block threads, blocks per SM, tile, frame in shared (0/1). */
 ivb_status ivb_get_tuning(ivb_problem* p, int32_t* block_threads, int32_t* blocks_per_sm,

@@ -86,6 +86,23 @@ extern "C" ivb_status ivb_propagate(const ivb_tape* tape, int32_t n_boxes, const
     return IVB_OK;
 }
 
+extern "C" ivb_status ivb_host_gradient(const ivb_tape* tape, const double* box, int32_t output, int32_t grad_mode,
+                                        double* G) {
+    if (!tape || !box || !G) return IVB_EINVAL;
+    if (!ivb::validate_tape(tape).empty()) return IVB_ETAPE;
+    if (output < 0 || output >= tape->n_outputs || (grad_mode != IVB_GRAD_FORWARD && grad_mode != IVB_GRAD_ADJOINT))
+        return IVB_EINVAL;
+    ivb::HostTape H;
+    ivb::host_tape(tape, H);
+    std::vector<ivb::hiv> g(H.n);
+    ivb::host_gradient(H, box, output, grad_mode, g.data());
+    for (int i = 0; i < H.n; ++i) {
+        G[2 * i] = g[i].lo;
+        G[2 * i + 1] = g[i].hi;
+    }
+    return IVB_OK;
+}
+
 extern "C" ivb_status ivb_bnb_solve(ivb_problem* p, int32_t n, const double* root, const ivb_bnb_options* o,
                                     ivb_bnb_result* res, void* stream_) {
     if (!p) return IVB_EINVAL;

@@ -67,6 +67,7 @@ double mul_dir(double a, double b, bool up) {
 // a / b for finite a and b != 0
 double div_dir(double a, double b, bool up) {
     const double q = a / b;
+    if (a == 0.0) return q;                  // exact (+-0)
     if (!std::isfinite(q)) return q > 0 ? (up ? q : DBL_MAX) : (up ? -DBL_MAX : q);
     if (std::fabs(q) < kTiny || std::fabs(a) < kTiny) return up ? nup(q) : ndn(q);
     // a - q b, exact: its sign (times the sign of b) says on which side of q the quotient lies

@@ -95,11 +95,12 @@ def lib() -> ctypes.CDLL:
         L.ivb_bnb_solve.argtypes = [P, I32, P, P, P, P]
         L.ivb_get_specialization.argtypes = [P, P, P, P, P, P]
         L.ivb_propagate.argtypes = [P, I32, P, D, I32, P, P]
+        L.ivb_host_gradient.argtypes = [P, P, I32, I32, P]
         L.ivb_specialize_compile.argtypes = [P, I32, I32, P, P, P]
         for f in ("ivb_create_problem", "ivb_bound_nodes", "ivb_bound_nodes_ex", "ivb_enclose", "ivb_point_grad",
                   "ivb_pick_splits", "ivb_get_tuning", "ivb_bnb_solve", "ivb_op_counts", "ivb_fp64_probe",
                   "ivb_bound_nodes_noalloc", "ivb_eval_op", "ivb_get_specialization", "ivb_specialize_compile",
-                  "ivb_propagate"):
+                  "ivb_propagate", "ivb_host_gradient"):
             getattr(L, f).restype = I32
         _lib = L
     return _lib
@@ -255,6 +256,15 @@ def ivb_propagate(tape, boxes, ub=float("inf"), passes=4):
     _check(lib().ivb_propagate(ctypes.byref(t), bx.shape[0], _ptr(bx), float(ub), int(passes), _ptr(out),
                                _ptr(inf)))
     return out, inf.astype(bool)
+
+
+def ivb_host_gradient(tape, box, output=0, grad_mode="adjoint"):
+    """gradient enclosure [n, 2] of one output over one box, on the host (no GPU)"""
+    bx = np.ascontiguousarray(box, dtype=np.float64).reshape(int(tape.n_vars), 2)
+    G = np.empty_like(bx)
+    t, keep = _c_tape(tape)
+    _check(lib().ivb_host_gradient(ctypes.byref(t), _ptr(bx), int(output), GRAD[grad_mode], _ptr(G)))
+    return G
 
 
 def ivb_last_error(problem=None) -> str:

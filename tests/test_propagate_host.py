@@ -61,3 +61,41 @@ def test_propagation_rejects_bad_input(ivb):
     assert e.value.status == ivb.IVB_ETAPE
     out, inf = ivb.ivb_propagate(t, np.zeros((0, 2, 2)))
     assert out.shape == (0, 2, 2) and inf.shape == (0,)
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("grad_mode", ["forward", "adjoint"])
+def test_host_gradient_bit_exact_rational(ivb, seed, grad_mode):
+    """the host gradient behind the B&B's descent corner (ivb_host_gradient)
+    equals the oracle's gradient enclosure over the same box bit for bit on
+    rational tapes, fused accumulation included, for every output"""
+    n = 3 + seed % 3
+    t = W.random_problem(n, 60, 2, W.OPS_RATIONAL, [[-3, 2]] * n, 700 + seed, "rational")
+    boxes = W.bisection_frontier(t.root_box, 40, seed=seed)
+    ones = np.ones(n, np.int32)
+    for box in boxes:
+        _, _, Go = oracle.enclose(t, box, ones, grad_mode=grad_mode, want_g=True)
+        for o in range(t.n_out):
+            Gh = ivb.ivb_host_gradient(t, box, o, grad_mode)
+            assert np.array_equal(Gh, Go[0, o]), (o, Gh, Go[0, o])
+
+
+@pytest.mark.parametrize("config", [1, 2])
+def test_host_gradient_contains_oracle_with_exp_log(ivb, config):
+    """with exp and log the host widens the C library's values by two ulps, so
+    its gradient enclosures contain the oracle's tight ones"""
+    t = W.config_tape(config)
+    boxes = W.bisection_frontier(t.root_box, 24, seed=config)
+    ones = np.ones(t.n_vars, np.int32)
+    for grad_mode in ("forward", "adjoint"):
+        for box in boxes:
+            _, _, Go = oracle.enclose(t, box, ones, grad_mode=grad_mode, want_g=True)
+            for o in range(t.n_out):
+                Gh = ivb.ivb_host_gradient(t, box, o, grad_mode)
+                assert np.all(Gh[:, 0] <= Go[0, o, :, 0]) and np.all(Gh[:, 1] >= Go[0, o, :, 1])
+
+
+def test_host_gradient_rejects_bad_arguments(ivb):
+    t = W.config_tape(1)
+    with pytest.raises(ivb.IvbError):
+        ivb.ivb_host_gradient(t, t.root_box, t.n_out, "adjoint")
