@@ -177,10 +177,12 @@ ivb_status ivb_bound_nodes_ex(ivb_problem* p, int32_t n_nodes, const double* box
  * device and can fail under memory pressure. The call makes no allocation:
  * the node queue, reduction keys, work counter and an error word live in one
  * file-scope device array of 512 KiB, per-thread frames in shared memory.
- *   - boxes, splits_per_dim, out_lb, out_infeasible: DEVICE arrays with the
- *     layouts of ivb_bound_nodes; 1 <= n_nodes <= IVB_NOALLOC_MAX_NODES
- *     (larger batches are rejected with IVB_EINVAL); problems whose
- *     per-thread frame does not fit in shared memory get IVB_ENOTSUP.
+ *   - boxes, splits_per_dim, out_lb, out_infeasible: DEVICE arrays of the
+ *     device the problem was created on, with the layouts of ivb_bound_nodes;
+ *     that device must be current (else IVB_EINVAL);
+ *     1 <= n_nodes <= IVB_NOALLOC_MAX_NODES (larger or empty batches are
+ *     rejected with IVB_EINVAL); problems whose per-thread frame does not fit
+ *     in shared memory get IVB_ENOTSUP.
  *   - the first call on a device looks up the array's device address with
  *     cudaGetSymbolAddress (with that device current); make that first call
  *     before any stream capture.
@@ -188,8 +190,10 @@ ivb_status ivb_bound_nodes_ex(ivb_problem* p, int32_t n_nodes, const double* box
  *     call's contents (each call resets what must start fixed: the counter,
  *     the keys and the error word); calls that overlap on the GPU race with
  *     each other, so order them (one stream, or events).
- *   - returns after the work completes: invalid boxes or splits, found on
- *     the device, are reported as IVB_EINVAL naming the first bad node.
+ *   - returns only after the work completes (it waits on cuda_stream):
+ *     invalid boxes or splits, found on the device, are reported as
+ *     IVB_EINVAL naming the first bad node; out_lb and out_infeasible are
+ *     then unspecified for every node of the call.
  *   - the array stays allocated on every GPU that loads the library until
  *     the process exits. */
 #define IVB_NOALLOC_MAX_NODES 256

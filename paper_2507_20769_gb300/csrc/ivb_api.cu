@@ -400,6 +400,7 @@ extern "C" ivb_status ivb_create_problem(const ivb_tape* tape, const ivb_options
     } while (0)
     int dev = 0;
     CKC(cudaGetDevice(&dev));
+    p->device = dev;
     CKC(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev));
     CKC(cudaDeviceGetAttribute(&p->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     for (int m = 0; m < 4; ++m) CKC(set_bound_smem_limit(m, p->smem_optin - 1024));

@@ -16,6 +16,7 @@ struct ivb_problem {
     ivb::HostProgram P{};
     ivb::HostTape host;       // the tape for host-side evaluation (B&B)
     int n = 0, n_out = 0, obj = 0;
+    int device = 0;           // the CUDA device current at creation (owns every buffer below)
     uint8_t out_kind[64]{};
     // program on the device
     ivb::ProgDesc* d_prog = nullptr;

@@ -69,7 +69,13 @@ __global__ void k_prepare_queue(const double* __restrict__ boxes, const int32_t*
             h[i] = bad ? 0.0 : __ddiv_rn(__dsub_rn(b, a), (double)k);
             N[i] = bad ? 1 : k;
         }
-        if (bad) { atomicMin(err, (unsigned long long)nd + 1); c = 1; }
+        if (bad) {
+            // a rejected node becomes the one-subdomain box [0,0]^n, so the
+            // kernels that still run on it read finite values only
+            for (int i = 0; i < n; ++i) { lo[i] = 0.0; hi[i] = 0.0; h[i] = 0.0; N[i] = 1; }
+            atomicMin(err, (unsigned long long)nd + 1);
+            c = 1;
+        }
         cnt[nd] = c;
     }
     __syncthreads();
@@ -99,10 +105,11 @@ ivb_status cuda_fail(ivb_problem* p, cudaError_t e, const char* where) {
         if (e_ != cudaSuccess) return cuda_fail(p, e_, #call);    \
     } while (0)
 
-bool on_device(const void* ptr) {
+// device memory of device `dev` (the problem's)
+bool on_device(const void* ptr, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) { cudaGetLastError(); return false; }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 }  // namespace
@@ -117,8 +124,16 @@ extern "C" ivb_status ivb_bound_nodes_noalloc(ivb_problem* p, int32_t n_nodes, c
                                        std::to_string(IVB_NOALLOC_MAX_NODES) + "] (fixed scratch capacity)");
     if (!boxes || !splits_per_dim || !out_lb || !out_infeasible)
         return fail(p, IVB_EINVAL, "ivb_bound_nodes_noalloc: all four arrays are required");
-    if (!on_device(boxes) || !on_device(splits_per_dim) || !on_device(out_lb) || !on_device(out_infeasible))
-        return fail(p, IVB_EINVAL, "ivb_bound_nodes_noalloc: every array must be device memory");
+    // the problem's program and kernel attributes belong to the device it was created on
+    int cur = -1;
+    CKN(cudaGetDevice(&cur));
+    if (cur != p->device)
+        return fail(p, IVB_EINVAL, "ivb_bound_nodes_noalloc: the current device (" + std::to_string(cur) +
+                                       ") is not the device the problem was created on (" +
+                                       std::to_string(p->device) + ")");
+    if (!on_device(boxes, cur) || !on_device(splits_per_dim, cur) || !on_device(out_lb, cur) ||
+        !on_device(out_infeasible, cur))
+        return fail(p, IVB_EINVAL, "ivb_bound_nodes_noalloc: every array must be device memory of the problem's device");
     const int mode = p->opt.grad_mode == IVB_GRAD_ADJOINT ? KM_ADJ_REDUCE : KM_FWD_REDUCE;
     const int fu = p->opt.grad_mode == IVB_GRAD_ADJOINT ? p->P.L.total_adj : p->P.L.total_fwd;
     // per-thread frames in shared memory: the largest block of 128, 64 or 32 threads that fits
@@ -133,8 +148,7 @@ extern "C" ivb_status ivb_bound_nodes_noalloc(ivb_problem* p, int32_t n_nodes, c
     if (bps < 1) return fail(p, IVB_ENOTSUP, "ivb_bound_nodes_noalloc: launch does not fit on an SM");
 
     // one-time set-up on this device: the device address of the scratch array
-    int dev = 0;
-    CKN(cudaGetDevice(&dev));
+    const int dev = cur;
     if (dev < 0 || dev >= kMaxDevices) return fail(p, IVB_ENOTSUP, "ivb_bound_nodes_noalloc: device index too large");
     if (!g_scratch_addr[dev]) {
         void* addr = nullptr;

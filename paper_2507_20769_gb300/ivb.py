@@ -342,10 +342,27 @@ class Problem:
     def ivb_bound_nodes_noalloc(self, boxes, splits, out_lb, out_infeasible, stream=None):
         """allocation-free bounding for callers that cannot allocate device
         memory: all four arguments are CUDA tensors (outputs preallocated)"""
+        import torch
         for x in (boxes, splits, out_lb, out_infeasible):
             if not (_is_torch(x) and x.is_cuda):
                 raise TypeError("ivb_bound_nodes_noalloc takes CUDA tensors only")
+        want = ((boxes, torch.float64, "boxes"), (splits, torch.int32, "splits"),
+                (out_lb, torch.float64, "out_lb"), (out_infeasible, torch.uint8, "out_infeasible"))
+        for x, dt, name in want:
+            if x.dtype != dt:
+                raise TypeError(f"{name} must be {dt}, got {x.dtype}")
+            if not x.is_contiguous():
+                raise ValueError(f"{name} must be contiguous")
+            if x.device != boxes.device:
+                raise ValueError(f"{name} is on {x.device}, boxes on {boxes.device}")
+        if boxes.ndim != 3 or boxes.shape[1:] != (self.n_vars, 2):
+            raise ValueError(f"boxes must have shape (nodes, {self.n_vars}, 2), got {tuple(boxes.shape)}")
         nn = int(boxes.shape[0])
+        if tuple(splits.shape) != (nn, self.n_vars):
+            raise ValueError(f"splits must have shape ({nn}, {self.n_vars}), got {tuple(splits.shape)}")
+        for x, name in ((out_lb, "out_lb"), (out_infeasible, "out_infeasible")):
+            if tuple(x.shape) != (nn,):
+                raise ValueError(f"{name} must have shape ({nn},), got {tuple(x.shape)}")
         s = stream if stream is not None else _stream_for(boxes)
         _check(lib().ivb_bound_nodes_noalloc(self._h, nn, _ptr(boxes), _ptr(splits), _ptr(out_lb),
                                              _ptr(out_infeasible), s), self._h)

@@ -3,8 +3,12 @@ cannot allocate device memory while they run: through the C ABI, its results
 must equal those of the regular ivb_bound_nodes on the same inputs, on two
 calls in a row (the fixed scratch keeps the previous call's contents, so the
 second call checks that everything that must be reset is reset). It rejects
-batches beyond its fixed capacity and non-device arrays."""
+batches beyond its fixed capacity, empty batches and host arrays in the C code
+itself, and the Python wrapper rejects wrong dtypes and short outputs before
+any device memory is touched."""
 from __future__ import annotations
+
+import ctypes
 
 import numpy as np
 import pytest
@@ -76,3 +80,57 @@ def test_noalloc_rejects_what_it_cannot_hold():
         p.ivb_bound_nodes_noalloc(bd[:4].contiguous(), sd[:4].contiguous(), lb[:4], inf[:4])
         ref, _ = p.bound_nodes(np.array([t.root_box] * 4), np.ones((4, t.n_vars), np.int32))
         assert np.array_equal(lb[:4].cpu().numpy(), ref)
+
+
+def test_noalloc_c_entry_rejects_host_arrays_and_empty_batches():
+    """called directly through ctypes, so the C-side checks are what answers"""
+    t = W.config_tape(1)
+    with ivb.Problem(t) as p:
+        f = ivb.lib().ivb_bound_nodes_noalloc
+        boxes = np.ascontiguousarray(np.array([t.root_box] * 4))
+        splits = np.ones((4, t.n_vars), np.int32)
+        lb_d = torch.empty(4, dtype=torch.float64, device=DEV)
+        inf_d = torch.empty(4, dtype=torch.uint8, device=DEV)
+        bd = torch.from_numpy(boxes).to(DEV)
+        sd = torch.from_numpy(splits).to(DEV)
+        vp = ctypes.c_void_p
+        # host boxes and splits (numpy pointers)
+        st = f(p._h, 4, vp(boxes.ctypes.data), vp(splits.ctypes.data), vp(lb_d.data_ptr()),
+               vp(inf_d.data_ptr()), None)
+        assert st == ivb.IVB_EINVAL and "device memory" in ivb.lib().ivb_last_error(p._h).decode()
+        # host output
+        lb_h = np.empty(4)
+        st = f(p._h, 4, vp(bd.data_ptr()), vp(sd.data_ptr()), vp(lb_h.ctypes.data), vp(inf_d.data_ptr()), None)
+        assert st == ivb.IVB_EINVAL and "device memory" in ivb.lib().ivb_last_error(p._h).decode()
+        # empty batch
+        st = f(p._h, 0, vp(bd.data_ptr()), vp(sd.data_ptr()), vp(lb_d.data_ptr()), vp(inf_d.data_ptr()), None)
+        assert st == ivb.IVB_EINVAL and "n_nodes" in ivb.lib().ivb_last_error(p._h).decode()
+        # the entry point still works afterwards
+        stream = ctypes.c_void_p(torch.cuda.current_stream(DEV).cuda_stream)
+        st = f(p._h, 4, vp(bd.data_ptr()), vp(sd.data_ptr()), vp(lb_d.data_ptr()), vp(inf_d.data_ptr()), stream)
+        assert st == ivb.IVB_OK
+        ref, _ = p.bound_nodes(boxes, splits)
+        assert np.array_equal(lb_d.cpu().numpy(), ref)
+
+
+def test_noalloc_wrapper_rejects_wrong_dtypes_and_short_outputs():
+    t = W.config_tape(1)
+    with ivb.Problem(t) as p:
+        bd = torch.tensor(np.array([t.root_box] * 4), device=DEV)
+        sd = torch.ones((4, t.n_vars), dtype=torch.int32, device=DEV)
+        lb = torch.empty(4, dtype=torch.float64, device=DEV)
+        inf = torch.empty(4, dtype=torch.uint8, device=DEV)
+        with pytest.raises(TypeError):
+            p.ivb_bound_nodes_noalloc(bd.float(), sd, lb, inf)
+        with pytest.raises(TypeError):
+            p.ivb_bound_nodes_noalloc(bd, sd, lb.float(), inf)
+        with pytest.raises(TypeError):
+            p.ivb_bound_nodes_noalloc(bd, sd.long(), lb, inf)
+        with pytest.raises(ValueError):
+            p.ivb_bound_nodes_noalloc(bd, sd, lb[:3], inf)
+        with pytest.raises(ValueError):
+            p.ivb_bound_nodes_noalloc(bd, sd, lb, inf[:2])
+        with pytest.raises(ValueError):
+            p.ivb_bound_nodes_noalloc(bd, sd[:, :1].contiguous(), lb, inf)
+        with pytest.raises(ValueError):
+            p.ivb_bound_nodes_noalloc(bd[:, :1].contiguous(), sd, lb, inf)
