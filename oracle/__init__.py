@@ -7,6 +7,11 @@ loads it, and it shares no code with the CUDA library.
 `build()` compiles ivb_oracle.c with gcc; `lib()` loads it (building on first
 use). The wrappers take a tape object with attributes n_vars, op, a, b, c,
 out_idx, out_kind (numpy arrays) and return numpy arrays.
+
+`tight` selects the exp/log enclosures: True / 1 binary128 evaluation rounded
+outward (within one ulp of the true value), False / 0 the libm result widened
+by two ulps (timing), an integer k > 1 the tight enclosure moved k - 1 further
+steps outward on each side (the outer end of a parity bracket).
 """
 from __future__ import annotations
 

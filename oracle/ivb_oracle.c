@@ -160,27 +160,39 @@ static double q_to_up(qreal q) { double d = (double)q; if ((qreal)d < q) d = nex
  * tight=1: evaluate in binary128, widen by 2^-104 relative (far above the
  *          library's quad error), round outward to double: at most one ulp
  *          from the true value per side.
- * tight=0: round-to-nearest libm result widened by two ulps per side. */
+ * tight=0: round-to-nearest libm result widened by two ulps per side.
+ * tight=k>1: the tight enclosure moved k-1 further representable steps
+ *          outward on each side -- the outer end of the bracket that parity
+ *          tests put around an implementation allowed k-1 steps beyond the
+ *          tight ends per operation; every other operation is unchanged, so
+ *          by inclusion isotonicity (Definition 2) a whole tape evaluated
+ *          with such operations lies between the tight=1 and tight=k sweeps. */
 static double exp_dn(double x, int tight) {
     if (isinf(x)) return x < 0 ? 0.0 : INFINITY;
     double r;
-    if (tight) { qreal q = Q_EXP((qreal)x); r = q_to_dn(q - q * Q_EPS); }
+    if (tight) { qreal q = Q_EXP((qreal)x); r = q_to_dn(q - q * Q_EPS); if (tight > 1) r = step_dn(r, tight - 1); }
     else r = step_dn(exp(x), 2);
     return r < 0.0 ? 0.0 : r;
 }
 static double exp_up(double x, int tight) {
     if (isinf(x)) return x < 0 ? 0.0 : INFINITY;
-    if (tight) { qreal q = Q_EXP((qreal)x); return q_to_up(q + q * Q_EPS); }
+    if (tight) { qreal q = Q_EXP((qreal)x); double r = q_to_up(q + q * Q_EPS); return tight > 1 ? step_up(r, tight - 1) : r; }
     return step_up(exp(x), 2);
 }
 static double log_dn(double x, int tight) { /* x > 0 */
     if (isinf(x)) return INFINITY;
-    if (tight) { qreal q = Q_LOG((qreal)x); qreal m = q < 0 ? -q : q; return q_to_dn(q - m * Q_EPS); }
+    if (tight) {
+        qreal q = Q_LOG((qreal)x); qreal m = q < 0 ? -q : q; double r = q_to_dn(q - m * Q_EPS);
+        return tight > 1 ? step_dn(r, tight - 1) : r;
+    }
     return step_dn(log(x), 2);
 }
 static double log_up(double x, int tight) { /* x > 0 */
     if (isinf(x)) return INFINITY;
-    if (tight) { qreal q = Q_LOG((qreal)x); qreal m = q < 0 ? -q : q; return q_to_up(q + m * Q_EPS); }
+    if (tight) {
+        qreal q = Q_LOG((qreal)x); qreal m = q < 0 ? -q : q; double r = q_to_up(q + m * Q_EPS);
+        return tight > 1 ? step_up(r, tight - 1) : r;
+    }
     return step_up(log(x), 2);
 }
 

@@ -274,6 +274,51 @@ def test_transcendental_enclosure_one_ulp(fn):
                 assert mpmath.mpf(float(_next_dn(h))) <= t              # upper end within one step
 
 
+@pytest.mark.parametrize("fn", ["exp", "log"])
+@pytest.mark.parametrize("k", [2, 5])
+def test_widened_bracket_is_k_minus_1_steps_beyond_tight(fn, k):
+    """tight=k > 1 moves each tight end exactly k-1 representable steps
+    outward (the exp lower end stays >= 0), counted here with numpy's own
+    nextafter, and still encloses the true value"""
+    rng = np.random.default_rng(12 + k)
+    if fn == "exp":
+        x = np.concatenate([rng.uniform(-30, 30, 300), [0.0, 1.0, -745.5, -800.0, 709.7, 710.0]])
+        lo, hi = oracle.exp_enclose(x, tight=True)
+        wlo, whi = oracle.exp_enclose(x, tight=k)
+    else:
+        x = np.concatenate([10.0 ** rng.uniform(-300, 300, 300), [1.0, 2.0, 0.5]])
+        lo, hi = oracle.log_enclose(x, tight=True)
+        wlo, whi = oracle.log_enclose(x, tight=k)
+    elo, ehi = lo.copy(), hi.copy()
+    for _ in range(k - 1):
+        elo = np.nextafter(elo, -np.inf)
+        ehi = np.nextafter(ehi, np.inf)
+    if fn == "exp":
+        elo = np.maximum(elo, 0.0)
+    assert np.array_equal(wlo, elo) and np.array_equal(whi, ehi)
+    assert np.all(wlo <= lo) and np.all(whi >= hi)
+
+
+@pytest.mark.parametrize("config", [1, 2])
+def test_widened_sweep_brackets_tight_sweep(config):
+    """every operation other than exp/log is the same in both modes, so by
+    isotonicity (Definition 2) the per-subdomain enclosures of the tight=5
+    sweep contain the tight ones (F, f(c) and G), and a tape without exp/log
+    gives identical bits"""
+    t = W.config_tape(config)
+    box = W.bisection_frontier(t.root_box, 4, seed=config)[1]
+    splits = np.array([3] * t.n_vars, np.int32)
+    F, Fc, G = oracle.enclose(t, box, splits, tight=True, want_fc=True, want_g=True)
+    F5, Fc5, G5 = oracle.enclose(t, box, splits, tight=5, want_fc=True, want_g=True)
+    for a, b in ((F, F5), (Fc, Fc5), (G, G5)):
+        assert np.all(b[..., 0] <= a[..., 0]) and np.all(b[..., 1] >= a[..., 1])
+    assert not np.array_equal(F, F5)
+    r = W.random_problem(3, 40, 1, W.OPS_RATIONAL, [[-2, 2]] * 3, 4242, "rational")
+    Fr, _, Gr = oracle.enclose(r, r.root_box, [3, 2, 4], tight=True, want_g=True)
+    Fr5, _, Gr5 = oracle.enclose(r, r.root_box, [3, 2, 4], tight=5, want_g=True)
+    assert np.array_equal(Fr, Fr5) and np.array_equal(Gr, Gr5)
+
+
 # ------------------------------------------------------------ tape sweeps
 
 def test_cubic_fig5_nie_textbook():

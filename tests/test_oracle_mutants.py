@@ -55,6 +55,12 @@ MUTANTS = [
     ("decode makes the last dimension fastest",
      "    for (int i = 0; i < n; ++i) {\n        const int64_t N = splits[i];",
      "    for (int ii = 0, i = n - 1; ii < n; ++ii, --i) {\n        const int64_t N = splits[i];"),
+    ("parity bracket of exp widens one step too few",
+     "r = q_to_dn(q - q * Q_EPS); if (tight > 1) r = step_dn(r, tight - 1); }",
+     "r = q_to_dn(q - q * Q_EPS); if (tight > 1) r = step_dn(r, tight - 2); }"),
+    ("parity bracket of log moves its upper end inward",
+     "        return tight > 1 ? step_up(r, tight - 1) : r;\n    }\n    return step_up(log(x), 2);",
+     "        return tight > 1 ? step_dn(r, tight - 1) : r;\n    }\n    return step_up(log(x), 2);"),
     ("subdomain endpoint off by one",
      "    double e = lo + (double)j * h;",
      "    double e = lo + (double)(j + 1) * h;"),
