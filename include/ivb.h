@@ -31,7 +31,7 @@
 extern "C" {
 #endif
 
-#define IVB_ABI_VERSION 1
+#define IVB_ABI_VERSION 2
 #define IVB_MAX_VARS 32        /* variables per problem */
 #define IVB_MAX_OUTPUTS 64     /* objective + constraints per problem */
 #define IVB_MAX_OPS 1048576    /* tape entries per problem */
@@ -116,9 +116,20 @@ typedef struct {
                                   and the long primitives are called out of
                                   line, which halves the compile time at the
                                   same speed; 2: the same fully inlined;
+                                  3: segmented -- the per-subdomain program
+                                  cut into short chunk functions of bounded
+                                  work and register use, values crossing
+                                  chunks kept in a per-thread state area in
+                                  device memory, the reverse sweep
+                                  recomputing its segment's forward values
+                                  from checkpoints (option recompute), chunks
+                                  compiled in parallel and linked (adjoint
+                                  mode only; for large tapes);
                                   0 (default): tape interpreter; -1: as 1 when
                                   the tape has at most 1024 interval
-                                  operations per subdomain, else interpret  */
+                                  operations per subdomain, else as 3 in
+                                  adjoint mode and the interpreter in forward
+                                  mode                                      */
     int32_t emulate;           /* tape-specialised kernel only: endpoint
                                   operations computed by an exact emulation
                                   on the integer pipes (bit-identical to the
@@ -128,6 +139,17 @@ typedef struct {
                                   ends of sums and differences, 8 lower ends;
                                   -1 (default): the library's choice, now 0
                                   (no gain inside the bounding kernel)     */
+    int32_t recompute;         /* segmented kernel: forward values of a
+                                  reverse chunk's own segment that are
+                                  recomputed from the segment's checkpoints
+                                  instead of read back from the state area:
+                                  0 none, 1 the cheap operations (+ - * sqr
+                                  neg; the values of / sqrt exp log are
+                                  stored), 2 all; -1 (default): 1           */
+    int32_t seg_chunk;         /* segmented kernel: estimated FP64 issue
+                                  slots per chunk (0 = default 320)         */
+    int32_t seg_regs;          /* segmented kernel: register budget of every
+                                  chunk function, 64..255 (0 = default 128) */
 } ivb_options;
 
 typedef struct ivb_problem ivb_problem;
@@ -314,10 +336,21 @@ ivb_status ivb_get_tuning(ivb_problem* p, int32_t* block_threads, int32_t* block
 ivb_status ivb_get_specialization(ivb_problem* p, int32_t* active, int32_t* registers,
                                   int32_t* local_bytes, double* compile_seconds, int32_t* emulate);
 
+/* The segmented kernel of a problem (specialize = 3; each may be NULL):
+ * doubles of per-thread state, chunk functions, state loads and stores per
+ * subdomain (intervals and centre coordinates), forward operations recomputed
+ * per subdomain by the reverse chunks, and the recomputation policy compiled
+ * in. Zeros when the problem has no segmented kernel. Not part of the
+ * paper's method: reports how the bounds are computed. */
+ivb_status ivb_get_segmentation(ivb_problem* p, int32_t* state_units, int32_t* chunks, int64_t* state_loads,
+                                int64_t* state_stores, int64_t* recomputed, int32_t* recompute);
+
 /* Generate and compile (NVRTC, sm_103a) the tape-specialised kernel of a
  * tape without loading it -- needs no GPU; compact = 1 as for specialize = 1,
- * 0 as for specialize = 2. Reports ptxas' registers per thread and
- * spill-store bytes, and the compile time (each may be NULL).
+ * 0 as for specialize = 2, 3 as for specialize = 3 (segmented, adjoint mode
+ * only, default segmentation options). Reports ptxas' registers per thread
+ * (the largest over the functions compiled) and spill-store bytes (summed),
+ * and the compile time (each may be NULL).
  * IVB_ETAPE for an invalid tape, IVB_ENOTSUP (message in ivb_last_error(NULL))
  * when the program does not compile. */
 ivb_status ivb_specialize_compile(const ivb_tape* tape, int32_t grad_mode, int32_t compact, int32_t* registers,

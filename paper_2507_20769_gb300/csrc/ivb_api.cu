@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/ivb.h"
@@ -54,8 +55,20 @@ int kernel_mode(const ivb_problem* p, bool store) {
     return store ? (adj ? KM_ADJ_STORE : KM_FWD_STORE) : (adj ? KM_ADJ_REDUCE : KM_FWD_REDUCE);
 }
 
+// per-thread frame of the tape interpreter (store modes, and the reduce mode
+// when no tape-specialised kernel is loaded)
 int frame_units(const ivb_problem* p) {
     return p->opt.grad_mode == IVB_GRAD_ADJOINT ? p->P.L.total_adj : p->P.L.total_fwd;
+}
+
+bool use_jit(const ivb_problem* p) { return p->jit.kern != nullptr; }
+
+// per-thread units of device memory the reduce kernel needs: the interpreter's
+// frame, a segmented kernel's state area, nothing for the other specialised
+// kernels (registers only)
+int reduce_units(const ivb_problem* p) {
+    if (!use_jit(p)) return frame_units(p);
+    return p->jit.state_units;
 }
 
 // Read host or device input arrays into host vectors (device arrays are
@@ -130,8 +143,8 @@ ivb_status stage_queue(ivb_problem* p, int n_nodes, const double* boxes, const i
     return IVB_OK;
 }
 
-ivb_status ensure_frame(ivb_problem* p, int grid, int block) {
-    const size_t need = (size_t)grid * block * frame_units(p) * sizeof(double);
+ivb_status ensure_frame(ivb_problem* p, int grid, int block, int units) {
+    const size_t need = (size_t)grid * block * units * sizeof(double);
     if (need <= p->frame_bytes) return IVB_OK;
     if (p->d_frame) cudaFree(p->d_frame);
     p->d_frame = nullptr;
@@ -151,7 +164,7 @@ KParams make_params(ivb_problem* p, int frame_smem) {
     K.tile = p->tile;
     K.gframe = p->d_frame;
     K.frame_in_smem = frame_smem;
-    K.frame_units = frame_units(p);
+    K.frame_units = reduce_units(p);
     K.keys = p->d_keys;
     K.form = p->opt.form;
     return K;
@@ -160,8 +173,6 @@ KParams make_params(ivb_problem* p, int frame_smem) {
 size_t smem_bytes(const ivb_problem* p, int block, int frame_smem) {
     return frame_smem ? (size_t)block * frame_units(p) * sizeof(double) : 0;
 }
-
-bool use_jit(const ivb_problem* p) { return p->jit.kern != nullptr; }
 
 // the reduce-mode bounding kernel: tape-specialised when compiled, else the interpreter
 cudaError_t launch_reduce(ivb_problem* p, const KParams& K, int grid, int block, int frame_smem, cudaStream_t s) {
@@ -243,7 +254,7 @@ ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
     ivb_status st = IVB_OK;
     for (const TuneCand& c : cands) {
         const int grid = p->sm_count * c.bps;
-        if (!use_jit(p)) st = ensure_frame(p, grid, c.block);
+        if (reduce_units(p) > 0) st = ensure_frame(p, grid, c.block, reduce_units(p));
         if (st) break;
         const int tile = c.block;   // one pass per grab: the smallest tail at the end of a launch
         for (int rep = 0; rep < 2 && !st; ++rep) {      // warm-up, then timed
@@ -317,6 +328,47 @@ ivb_status deliver(ivb_problem* p, int n_nodes, double* out_lb, uint8_t* out_inf
 // ======================================================================= ABI
 
 // generate, compile and load the tape-specialised reduce kernel
+// segmentation options of a problem
+SegPolicy seg_policy(const ivb_options& o) {
+    SegPolicy pol;
+    if (o.recompute >= 0) pol.recompute = o.recompute;
+    if (o.seg_chunk > 0) pol.chunk_cost = o.seg_chunk;
+    if (o.seg_regs > 0) pol.max_regs = o.seg_regs;
+    const unsigned hc = std::thread::hardware_concurrency();
+    pol.units = std::max(1, std::min(64, hc ? (int)hc : 8));
+    return pol;
+}
+
+// blocks of kJitBlockMax threads per SM that a register budget allows
+int seg_min_blocks(int max_regs) { return std::max(1, std::min(8, 65536 / (kJitBlockMax * max_regs))); }
+
+cudaError_t specialize_seg(ivb_problem* p, const std::vector<Ins>& ins, const std::vector<RIns>& rins,
+                           const std::vector<double>& consts, std::string* msg) {
+    const int emu = p->opt.emulate >= 0 ? p->opt.emulate : kJitDefaultEmulate;
+    const SegPolicy pol = seg_policy(p->opt);
+    const SegSource src = jit_seg_source(p->P, ins, rins, consts, kJitBlockMax, seg_min_blocks(pol.max_regs), emu,
+                                         p->opt.form, pol);
+    std::vector<char> cubin;
+    std::string tables;
+    double secs = 0.0;
+    *msg = jit_seg_compile(src, pol.max_regs, cubin, tables, &secs, nullptr, nullptr);
+    if (!msg->empty()) return cudaSuccess;
+    const cudaError_t ce = jit_load(cubin, tables, p->jit);
+    if (ce != cudaSuccess) return ce;
+    p->jit.mode = KM_ADJ_REDUCE;
+    p->jit.emulate = emu;
+    p->jit.compact = true;
+    p->jit.block_max = kJitBlockMax;
+    p->jit.compile_seconds = secs;
+    p->jit.state_units = src.state_units;
+    p->jit.chunks = src.chunks;
+    p->jit.state_loads = src.loads;
+    p->jit.state_stores = src.stores;
+    p->jit.recomputed = src.recomputed;
+    p->jit.recompute = pol.recompute;
+    return cudaSuccess;
+}
+
 cudaError_t specialize(ivb_problem* p, const std::vector<Ins>& ins, const std::vector<RIns>& rins,
                        const std::vector<double>& consts, int mode, std::string* msg) {
     const int emu = p->opt.emulate >= 0 ? p->opt.emulate : kJitDefaultEmulate;
@@ -353,6 +405,9 @@ extern "C" void ivb_options_default(ivb_options* o) {
     o->frame_in_shared = -1;
     o->specialize = 0;
     o->emulate = -1;
+    o->recompute = -1;
+    o->seg_chunk = 0;
+    o->seg_regs = 0;
 }
 
 extern "C" ivb_status ivb_create_problem(const ivb_tape* tape, const ivb_options* opt, ivb_problem** out) {
@@ -369,7 +424,13 @@ extern "C" ivb_status ivb_create_problem(const ivb_tape* tape, const ivb_options
     if (o.max_nodes < 1 || o.max_nodes > (1 << 20)) return fail(nullptr, IVB_EINVAL, "max_nodes must be in [1, 2^20]");
     if (o.block_threads < 0 || o.block_threads > 512 || (o.block_threads % 32))
         return fail(nullptr, IVB_EINVAL, "block_threads must be a multiple of 32 up to 512 (0 = auto)");
-    if (o.specialize < -1 || o.specialize > 2) return fail(nullptr, IVB_EINVAL, "specialize must be -1, 0, 1 or 2");
+    if (o.specialize < -1 || o.specialize > 3) return fail(nullptr, IVB_EINVAL, "specialize must be -1, 0, 1, 2 or 3");
+    if (o.specialize == 3 && o.grad_mode != IVB_GRAD_ADJOINT)
+        return fail(nullptr, IVB_EINVAL, "specialize = 3 (segmented) needs grad_mode IVB_GRAD_ADJOINT");
+    if (o.recompute < -1 || o.recompute > 2) return fail(nullptr, IVB_EINVAL, "recompute must be -1, 0, 1 or 2");
+    if (o.seg_chunk < 0 || o.seg_chunk > 100000) return fail(nullptr, IVB_EINVAL, "seg_chunk must be in [0, 100000]");
+    if (o.seg_regs != 0 && (o.seg_regs < 64 || o.seg_regs > 255))
+        return fail(nullptr, IVB_EINVAL, "seg_regs must be 0 or in [64, 255]");
     if (o.emulate < -1 || o.emulate > 15) return fail(nullptr, IVB_EINVAL, "emulate must be -1 or a bitmask in [0, 15]");
     if (o.specialize && o.block_threads > kJitBlockMax)
         return fail(nullptr, IVB_EINVAL, "block_threads above 256 with a tape-specialised kernel");
@@ -456,10 +517,13 @@ extern "C" ivb_status ivb_create_problem(const ivb_tape* tape, const ivb_options
         const int64_t* cnt = o.grad_mode == IVB_GRAD_ADJOINT ? p->P.cnt_adj : p->P.cnt_fwd;
         long long ops = 0;
         for (int k = 0; k < IVB_CNT_N; ++k) ops += cnt[k];
-        if (o.specialize >= 1 || ops / 2 <= kJitAutoMaxOps) {
+        const bool small = ops / 2 <= kJitAutoMaxOps;
+        const bool seg = o.specialize == 3 || (o.specialize == -1 && !small && o.grad_mode == IVB_GRAD_ADJOINT);
+        if (o.specialize >= 1 || small || seg) {
             const int mode = o.grad_mode == IVB_GRAD_ADJOINT ? KM_ADJ_REDUCE : KM_FWD_REDUCE;
             std::string msg;
-            const cudaError_t ce = specialize(p, ins, rins, consts, mode, &msg);
+            const cudaError_t ce = seg ? specialize_seg(p, ins, rins, consts, &msg)
+                                       : specialize(p, ins, rins, consts, mode, &msg);
             if (ce != cudaSuccess || !msg.empty()) {
                 jit_unload(p->jit);
                 if (o.specialize >= 1) {
@@ -533,7 +597,7 @@ ivb_status bound_nodes_impl(ivb_problem* p, int32_t n_nodes, const double* boxes
             const long long S = o2[1];
             const long long tiles = (S + p->block - 1) / p->block;
             const int grid = (int)std::min<long long>(tiles, (long long)p->sm_count * p->bps);
-            if (!use_jit(p)) st = ensure_frame(p, grid, p->block);
+            if (reduce_units(p) > 0) st = ensure_frame(p, grid, p->block, reduce_units(p));
             if (st) return st;
             CK(launch_init_keys(p->d_keys, p->d_queue, 1, p->n_out, s));
             CK(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned long long), s));
@@ -562,7 +626,7 @@ ivb_status bound_nodes_impl(ivb_problem* p, int32_t n_nodes, const double* boxes
             if (st) return st;
         }
         const int grid = p->sm_count * p->bps;
-        if (!use_jit(p)) st = ensure_frame(p, grid, p->block);
+        if (reduce_units(p) > 0) st = ensure_frame(p, grid, p->block, reduce_units(p));
         if (st) return st;
         if (p->opt.use_graph) {
             if (!p->gexec) {
@@ -626,9 +690,10 @@ extern "C" ivb_status ivb_enclose(ivb_problem* p, const double* box, const int32
     CK(cudaMemcpyAsync(p->d_counter, &first_u, sizeof(first_u), cudaMemcpyHostToDevice, s));
     const long long tiles = (count + p->block - 1) / p->block;
     const int grid = (int)std::min<long long>(tiles, (long long)p->sm_count * p->bps);
-    st = ensure_frame(p, grid, p->block);
+    st = ensure_frame(p, grid, p->block, frame_units(p));
     if (st) return st;
     KParams K = make_params(p, p->frame_smem);
+    K.frame_units = frame_units(p);
     K.tile = p->block;
     K.outF = dF ? out_F : tF;
     K.outFc = out_Fc ? (dFc ? out_Fc : tFc) : nullptr;
@@ -759,6 +824,20 @@ extern "C" ivb_status ivb_get_specialization(ivb_problem* p, int32_t* active, in
     return IVB_OK;
 }
 
+extern "C" ivb_status ivb_get_segmentation(ivb_problem* p, int32_t* state_units, int32_t* chunks,
+                                           int64_t* state_loads, int64_t* state_stores, int64_t* recomputed,
+                                           int32_t* recompute) {
+    if (!p) return fail(nullptr, IVB_EINVAL, "problem handle is NULL");
+    const bool seg = use_jit(p) && p->jit.state_units > 0;
+    if (state_units) *state_units = seg ? p->jit.state_units : 0;
+    if (chunks) *chunks = seg ? p->jit.chunks : 0;
+    if (state_loads) *state_loads = seg ? p->jit.state_loads : 0;
+    if (state_stores) *state_stores = seg ? p->jit.state_stores : 0;
+    if (recomputed) *recomputed = seg ? p->jit.recomputed : 0;
+    if (recompute) *recompute = seg ? p->jit.recompute : 0;
+    return IVB_OK;
+}
+
 extern "C" ivb_status ivb_specialize_compile(const ivb_tape* tape, int32_t grad_mode, int32_t compact,
                                              int32_t* registers, int32_t* spill_bytes, double* seconds) {
     std::string e = validate_tape(tape);
@@ -772,12 +851,23 @@ extern "C" ivb_status ivb_specialize_compile(const ivb_tape* tape, int32_t grad_
     e = compile_tape(tape, P, ins, rins, consts);
     if (!e.empty()) return fail(nullptr, IVB_ENOTSUP, e);
     const int mode = grad_mode == IVB_GRAD_ADJOINT ? KM_ADJ_REDUCE : KM_FWD_REDUCE;
-    const std::string src =
-        jit_source(P, ins, rins, consts, mode, kJitBlockMax, kJitMinBlocks, kJitDefaultEmulate, compact != 0, 0);
     std::vector<char> cubin;
     std::string tables;
     int regs = 0, spill = 0;
-    e = jit_compile(src, cubin, tables, seconds, &regs, &spill);
+    if (compact == 3) {
+        if (grad_mode != IVB_GRAD_ADJOINT)
+            return fail(nullptr, IVB_EINVAL, "the segmented kernel needs grad_mode IVB_GRAD_ADJOINT");
+        ivb_options o;
+        ivb_options_default(&o);
+        const SegPolicy pol = seg_policy(o);
+        const SegSource src = jit_seg_source(P, ins, rins, consts, kJitBlockMax, seg_min_blocks(pol.max_regs),
+                                             kJitDefaultEmulate, 0, pol);
+        e = jit_seg_compile(src, pol.max_regs, cubin, tables, seconds, &regs, &spill);
+    } else {
+        const std::string src =
+            jit_source(P, ins, rins, consts, mode, kJitBlockMax, kJitMinBlocks, kJitDefaultEmulate, compact != 0, 0);
+        e = jit_compile(src, cubin, tables, seconds, &regs, &spill);
+    }
     if (!e.empty()) return fail(nullptr, IVB_ENOTSUP, e);
     if (registers) *registers = regs;
     if (spill_bytes) *spill_bytes = spill;

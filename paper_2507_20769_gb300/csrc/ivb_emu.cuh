@@ -27,10 +27,10 @@
 
 namespace ivb {
 
-__device__ __noinline__ double mul_rd_hw(double x, double y) { return __dmul_rd(x, y); }
-__device__ __noinline__ double mul_ru_hw(double x, double y) { return __dmul_ru(x, y); }
-__device__ __noinline__ double add_rd_hw(double x, double y) { return __dadd_rd(x, y); }
-__device__ __noinline__ double add_ru_hw(double x, double y) { return __dadd_ru(x, y); }
+static __device__ __noinline__ double mul_rd_hw(double x, double y) { return __dmul_rd(x, y); }
+static __device__ __noinline__ double mul_ru_hw(double x, double y) { return __dmul_ru(x, y); }
+static __device__ __noinline__ double add_rd_hw(double x, double y) { return __dadd_rd(x, y); }
+static __device__ __noinline__ double add_ru_hw(double x, double y) { return __dadd_ru(x, y); }
 
 // x * y rounded toward +inf (up) or -inf; ok = false when an operand is not
 // a normal number or the exponent of the result leaves [1, 2046]

@@ -43,7 +43,9 @@ struct MathTables {
     ExpEntry exp[kExpTab];
     LogEntry log[kLogTab];
 };
-#ifdef __CUDACC_RTC__
+#if defined(__CUDACC_RTC__) && defined(IVB_JIT_EXTERN_TABLES)
+extern __device__ MathTables g_math;   // defined by the kernel unit of a segmented module
+#elif defined(__CUDACC_RTC__)
 __device__ MathTables g_math;          // run-time compiled module: filled from the library's copy
 #else
 static __device__ MathTables g_math;
@@ -88,11 +90,11 @@ __device__ __forceinline__ long long rem_sig(double a, double b, double c, int s
 
 // Slow paths out of line: inlined, the compiler would start parts of them
 // speculatively on the fast path, which costs FP64 issue slots every call.
-__device__ __noinline__ double rcp_slow(double y, bool up) { return up ? __drcp_ru(y) : __drcp_rd(y); }
-__device__ __noinline__ double div_slow(double x, double y, bool up) { return up ? __ddiv_ru(x, y) : __ddiv_rd(x, y); }
-__device__ __noinline__ double sqrt_slow(double x, bool up) { return up ? __dsqrt_ru(x) : __dsqrt_rd(x); }
-__device__ __noinline__ double exp_slow(double x) { return exp(x); }
-__device__ __noinline__ double log_slow(double x) { return log(x); }
+static __device__ __noinline__ double rcp_slow(double y, bool up) { return up ? __drcp_ru(y) : __drcp_rd(y); }
+static __device__ __noinline__ double div_slow(double x, double y, bool up) { return up ? __ddiv_ru(x, y) : __ddiv_rd(x, y); }
+static __device__ __noinline__ double sqrt_slow(double x, bool up) { return up ? __dsqrt_ru(x) : __dsqrt_rd(x); }
+static __device__ __noinline__ double exp_slow(double x) { return exp(x); }
+static __device__ __noinline__ double log_slow(double x) { return log(x); }
 
 // 1/y seed for y > 0 with biased exponent E in [1, 2044]: relative error < 2^-21
 __device__ __forceinline__ double rcp_seed(double y) {

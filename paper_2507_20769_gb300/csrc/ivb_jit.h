@@ -40,7 +40,38 @@ struct JitKernel {
     bool compact = false;      // long primitives called out of line
     int regs = 0, local_bytes = 0, max_threads = 0;
     double compile_seconds = 0.0;
+    // segmented kernels (ivb_jit_seg.cpp): per-thread state area in doubles
+    // (0 for the other variants), chunks, state loads and stores and
+    // recomputed forward operations per subdomain, recomputation policy
+    int state_units = 0, chunks = 0, recompute = -1;
+    long long state_loads = 0, state_stores = 0, recomputed = 0;
 };
+
+// Segmented kernels for large tapes (ivb_jit_seg.cpp): the per-subdomain
+// program cut into chunk functions of bounded estimated work, values that
+// cross chunks in a per-thread state area, reverse chunks recomputing their
+// segment's forward values (policy 0: none, stored; 1: the cheap operations
+// + - * sqr neg; 2: all), chunks compiled in `units` parallel NVRTC programs
+// and linked with nvJitLink.
+struct SegPolicy {
+    double chunk_cost = 320.0;   // estimated FP64 issue slots per chunk
+    int chunk_stmts = 96;        // statements per chunk
+    int recompute = 1;
+    int units = 16;
+    int max_regs = 128;          // register budget of every chunk function
+};
+struct SegSource {
+    std::string kernel;               // tile loop, Step 1, chunk calls, Step 3
+    std::vector<std::string> units;   // the chunk functions
+    int state_units = 0, chunks = 0;
+    long long loads = 0, stores = 0, recomputed = 0;
+};
+SegSource jit_seg_source(const HostProgram& P, const std::vector<Ins>& ins, const std::vector<RIns>& rins,
+                         const std::vector<double>& consts, int block_max, int min_blocks, int emulate, int form,
+                         const SegPolicy& pol);
+// compile the units in parallel and link them; "" on success
+std::string jit_seg_compile(const SegSource& src, int max_regs, std::vector<char>& cubin, std::string& tables_name,
+                            double* seconds, int* registers, int* spill_bytes);
 
 // CUDA C++ of the reduce-mode bounding kernel for this program; form 1 (the
 // natural interval extension alone) leaves out the gradient sweeps

@@ -36,7 +36,8 @@ class ivb_options(ctypes.Structure):
                 ("batched", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("max_nodes", ctypes.c_int32), ("frame_in_shared", ctypes.c_int32), ("specialize", ctypes.c_int32),
-                ("emulate", ctypes.c_int32)]
+                ("emulate", ctypes.c_int32), ("recompute", ctypes.c_int32), ("seg_chunk", ctypes.c_int32),
+                ("seg_regs", ctypes.c_int32)]
 
 
 class ivb_tape(ctypes.Structure):
@@ -97,9 +98,11 @@ def lib() -> ctypes.CDLL:
         L.ivb_propagate.argtypes = [P, I32, P, D, I32, P, P]
         L.ivb_host_gradient.argtypes = [P, P, I32, I32, P]
         L.ivb_specialize_compile.argtypes = [P, I32, I32, P, P, P]
+        L.ivb_get_segmentation.argtypes = [P, P, P, P, P, P, P]
         for f in ("ivb_create_problem", "ivb_bound_nodes", "ivb_bound_nodes_ex", "ivb_enclose", "ivb_point_grad",
                   "ivb_pick_splits", "ivb_get_tuning", "ivb_bnb_solve", "ivb_op_counts", "ivb_fp64_probe",
                   "ivb_bound_nodes_noalloc", "ivb_eval_op", "ivb_get_specialization", "ivb_specialize_compile",
+                  "ivb_get_segmentation",
                   "ivb_propagate", "ivb_host_gradient"):
             getattr(L, f).restype = I32
         _lib = L
@@ -222,9 +225,11 @@ def ivb_eval_op(opcode: int, x, y=None, acc=None):
     return r
 
 
-def ivb_specialize_compile(tape, grad_mode="adjoint", compact=True) -> dict:
+def ivb_specialize_compile(tape, grad_mode="adjoint", compact=True, variant=None) -> dict:
     """generate and compile (NVRTC, no GPU needed) the tape-specialised
-    kernel of a tape: ptxas registers, spill-store bytes, compile seconds"""
+    kernel of a tape: ptxas registers, spill-store bytes, compile seconds.
+    variant: the `specialize` value it is built as (1 compact, 2 inlined,
+    3 segmented); by default 1 or 2 from `compact`"""
     recs = tape.records()
     oi = np.ascontiguousarray(tape.out_idx, dtype=np.int32)
     ok = np.ascontiguousarray(tape.out_kind, dtype=np.uint8)
@@ -232,7 +237,8 @@ def ivb_specialize_compile(tape, grad_mode="adjoint", compact=True) -> dict:
                  ok.ctypes.data)
     regs, spill, secs = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
     g = GRAD[grad_mode] if isinstance(grad_mode, str) else int(grad_mode)
-    _check(lib().ivb_specialize_compile(ctypes.byref(t), g, int(bool(compact)), ctypes.byref(regs),
+    code = {1: 1, 2: 0, 3: 3}[int(variant)] if variant is not None else int(bool(compact))
+    _check(lib().ivb_specialize_compile(ctypes.byref(t), g, code, ctypes.byref(regs),
                                         ctypes.byref(spill), ctypes.byref(secs)))
     return {"registers": regs.value, "spill_bytes": spill.value, "seconds": secs.value}
 
@@ -426,6 +432,14 @@ class Problem:
         return {"active": bool(a.value), "registers": r.value, "local_bytes": lb.value, "compile_seconds": sec.value,
                 "emulate": em.value}
 
+    def ivb_get_segmentation(self) -> dict:
+        su, ch, rc = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        ld, stv, re = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().ivb_get_segmentation(self._h, ctypes.byref(su), ctypes.byref(ch), ctypes.byref(ld),
+                                          ctypes.byref(stv), ctypes.byref(re), ctypes.byref(rc)), self._h)
+        return {"state_units": su.value, "chunks": ch.value, "state_loads": ld.value, "state_stores": stv.value,
+                "recomputed": re.value, "recompute": rc.value}
+
     def ivb_op_counts(self) -> dict:
         c = (ctypes.c_int64 * 8)()
         _check(lib().ivb_op_counts(self._h, c), self._h)
@@ -445,6 +459,7 @@ class Problem:
     bnb_solve = ivb_bnb_solve
     get_tuning = ivb_get_tuning
     get_specialization = ivb_get_specialization
+    get_segmentation = ivb_get_segmentation
     launch_count = ivb_launch_count
     op_counts = ivb_op_counts
     bound_nodes_noalloc = ivb_bound_nodes_noalloc

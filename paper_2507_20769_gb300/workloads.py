@@ -469,6 +469,20 @@ def bisection_frontier(root_box, n_nodes: int, seed: int):
     return np.stack(boxes)
 
 
+def full_scale_splits(box, root_box, wide: int = 8, rest: int = 4, n_wide: int = 2) -> np.ndarray:
+    """Per-dimension split counts of one node of the full-scale workload
+    (n = 8, 2^18 subdomains per node, 64 nodes = 2^24 per B&B iteration):
+    `wide` on the `n_wide` dimensions of largest width relative to the root
+    box (ties: lowest index), `rest` elsewhere -- 8^2 * 4^6 = 2^18."""
+    box = np.asarray(box, dtype=np.float64)
+    root_box = np.asarray(root_box, dtype=np.float64)
+    rel = (box[:, 1] - box[:, 0]) / (root_box[:, 1] - root_box[:, 0])
+    order = sorted(range(box.shape[0]), key=lambda i: (-rel[i], i))
+    out = np.full(box.shape[0], rest, np.int32)
+    out[order[:n_wide]] = wide
+    return out
+
+
 def sample_points(box, count: int, seed: int) -> np.ndarray:
     """count points uniform in a box [n][2]"""
     rng = Xoshiro256ss(seed)

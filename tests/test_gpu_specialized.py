@@ -150,15 +150,20 @@ def test_specialized_full_size_config2_identical_to_interpreter(emulate, spec_mo
 
 
 def test_specialize_auto_info_and_empty_batch():
-    """specialize=-1 compiles a small tape and leaves a large one (configuration
-    5, above the size limit) to the interpreter; an empty batch is a no-op"""
+    """specialize=-1 compiles a small tape as one program; a large one
+    (configuration 4, above the size limit) gets the segmented kernel in
+    adjoint mode and the interpreter in forward mode; an empty batch is a
+    no-op"""
     with ivb.Problem(W.config_tape(1), specialize=-1) as p:
         info = p.get_specialization()
         assert info["active"] and 0 < info["registers"] <= 128 and info["compile_seconds"] > 0
+        assert p.get_segmentation()["chunks"] == 0
         r = p.bound_nodes_ex(np.zeros((0, 2, 2)), np.zeros((0, 2), np.int32))
         assert r["lb"].shape == (0,)
-    with ivb.Problem(W.config_tape(5), specialize=-1) as p:
+    with ivb.Problem(W.config_tape(4), specialize=-1, grad_mode="forward") as p:
         assert not p.get_specialization()["active"]
+    with ivb.Problem(W.config_tape(4), specialize=-1, grad_mode="adjoint") as p:
+        assert p.get_specialization()["active"] and p.get_segmentation()["chunks"] > 1
     with ivb.Problem(W.config_tape(1)) as p:
         assert not p.get_specialization()["active"]
 
