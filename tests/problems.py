@@ -220,3 +220,16 @@ def np_eval(tape, X):
             elif op == OP_NEG: r = -v[a]
             v.append(r)
     return np.stack([v[int(o)] for o in tape.out_idx], axis=1)
+
+
+def rational_tape_for_shards():
+    """seeded rational problem with constraints (n=3, objective + 2
+    inequalities of 50 entries) for the multi-rank host-path test"""
+    from paper_2507_20769_gb300 import workloads as W
+    return W.random_problem(3, 50, 2, W.OPS_RATIONAL, [[-3, 2]] * 3, 313, "rational shards")
+
+
+def shard_boxes(t, n_nodes=11):
+    """a bisection frontier of the root box, one shard item per node"""
+    from paper_2507_20769_gb300 import workloads as W
+    return W.bisection_frontier(t.root_box, n_nodes, seed=8)
