@@ -1,17 +1,27 @@
 #!/usr/bin/env python
 """Benchmark of GPU Subdomain Lower Bounding (interval Mean Value Form) on GB300.
 
-One step = Steps 1-3 (Section 3.1) for one batch of B&B nodes of the
-configuration-2 workload (n = 4, objective + 3 inequality constraints, seeded
-60-entry tapes with all eight intrinsics, box [-5,5]^4, 16^4 = 65536 subdomains
-per node), in one persistent launch replayed as a CUDA graph, adjoint gradients.
-Metric: subdomain bounds per second = subdomains x outputs enclosed per second.
+One step = Steps 1-3 (Section 3.1) for one B&B iteration of the full-scale
+workload: n = 8, objective + 10 inequality constraints, each a seeded
+1000-entry tape with + - * / sqr sqrt exp log on guarded domains, box
+[-10,10]^8; 64 B&B nodes of a bisection frontier, each split into
+8^2 * 4^6 = 2^18 subdomains (2^24 subdomains per step, 11 outputs each), in
+one persistent launch replayed as a CUDA graph, adjoint gradients, the
+library's choice of bounding kernel (segmented tape-specialised for these
+tapes). Metric: subdomain bounds per second = subdomains x outputs enclosed
+per second.
 
-Also printed: the roofline of the bounding kernel against the FP64 pipe peak
-measured live, the oracle on the host cores (cpu_baseline), the same metric end
-to end through host buffers (e2e), GPU clocks sampled during the timed region,
-and B&B wall clock to relative gap 1e-3 for the adjoint+batched path and the
-plain forward-mode one-node-per-launch path (time-capped).
+Also printed: the roofline of the bounding kernel (algorithmic endpoint
+operations per second against the FP64 pipe's peak from unit counts and the
+sampled clock, and the issue-slot view beside it), the oracle on the host
+cores on a bounded sample of the same workload (cpu_baseline), the same metric
+end to end through host buffers (e2e), GPU clocks sampled during the timed
+region, the plain-path configuration-2 step of earlier measurements, B&B
+wall clock to each configuration's gap (configurations 1, 2, 3 and 5; adjoint
++ batched against the plain forward-mode one-node-per-launch path,
+time-capped, final gap reported at the cap) with the oracle-backed B&B on the
+host cores beside configurations 1 and 2, and the two training-system
+patterns (adjoint vs forward tangents, batched vs per-node launches).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 N > 1 runs under torchrun, one process per GPU, each rank bounding its own
@@ -42,46 +52,49 @@ UNIT = "subdomain-bounds/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--nodes", type=int, default=64, help="nodes per step per GPU")
-    ap.add_argument("--bnb", type=int, default=1, help="run the B&B time-to-gap comparison (rank 0)")
-    ap.add_argument("--bnb-time", type=float, default=45.0, help="time cap per B&B run, seconds")
-    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target oracle sample time")
-    ap.add_argument("--bnb-configs", type=str, default="",
-                    help="comma list of configurations (2, 3, 5) for a B&B time-to-gap study with the host "
-                         "additions switched on one by one (minutes; off by default)")
-    ap.add_argument("--bnb-config-cap", type=float, default=90.0, help="time cap per run of that study, seconds")
-    ap.add_argument("--oracle-bnb", type=float, default=0.0,
-                    help="> 0: also run the oracle-backed B&B (host cores) on configurations 1 and 2 with this "
-                         "time cap in seconds (off by default)")
-    ap.add_argument("--specialize", type=int, default=1,
-                    help="1: tape-specialised bounding kernel (NVRTC at problem creation); 0: tape interpreter")
+    ap.add_argument("--nodes", type=int, default=64, help="B&B nodes per step per GPU (2^18 subdomains each)")
+    ap.add_argument("--specialize", type=int, default=-1,
+                    help="bounding kernel: -1 the library's choice (segmented for these tapes), 0 interpreter, "
+                         "1 compact, 3 segmented")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end measurement")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target oracle sample time")
+    ap.add_argument("--bnb", type=int, default=1, help="B&B time-to-gap comparisons (rank 0)")
+    ap.add_argument("--bnb-configs", type=str, default="1,2,3,5", help="configurations of the B&B comparison")
+    ap.add_argument("--bnb-cap", type=float, default=20.0, help="time cap per B&B run, seconds")
+    ap.add_argument("--bnb-cap5", type=float, default=30.0, help="time cap per B&B run on configuration 5")
+    ap.add_argument("--oracle-bnb", type=float, default=15.0,
+                    help="time cap of the oracle-backed B&B on configurations 1 and 2 (0: skip)")
+    ap.add_argument("--secondary", type=int, default=1, help="also time the configuration-2 step")
     ap.add_argument("--patterns", type=int, default=1,
                     help="also time adjoint vs forward (configuration 4) and batched vs per-node (configuration 3)")
     return ap.parse_args()
 
 
 def workload(rank: int, world: int, nodes: int):
+    """full-scale step: `nodes` frontier nodes per rank, 2^18 subdomains each"""
     from paper_2507_20769_gb300 import shard
     from paper_2507_20769_gb300 import workloads as W
-    wl = W.config_workload(2)
+    wl = W.config_workload(5)
     t = wl.tape
     boxes_all = W.bisection_frontier(t.root_box, nodes * world, seed=2026)
     b, e = shard.shard_range(nodes * world, rank, world)
     boxes = np.ascontiguousarray(boxes_all[b:e])
-    splits = np.ascontiguousarray(np.tile(wl.splits, (boxes.shape[0], 1)).astype(np.int32))
+    splits = np.ascontiguousarray(np.array([W.full_scale_splits(x, t.root_box) for x in boxes], np.int32))
     return wl, t, boxes, splits
 
 
 def workload_desc(nodes, world):
-    return {"workload": "configuration 2: n=4, objective + 3 inequality constraints, seeded 60-entry tapes "
-                        "(+ - * / sqr sqrt exp log on guarded domains), box [-5,5]^4, 16^4 = 65536 subdomains "
-                        "per node, batch of B&B nodes from a bisection frontier",
-            "nodes_per_step_per_gpu": nodes, "subdomains_per_node": 65536, "outputs": 4,
+    return {"workload": "configuration 5 (full scale): n=8, objective + 10 inequality constraints, seeded "
+                        "1000-entry tapes (+ - * / sqr sqrt exp log on guarded domains), box [-10,10]^8; one B&B "
+                        "iteration = 64 nodes of a bisection frontier x 2^18 subdomains (8^2 * 4^6 per node) "
+                        "= 2^24 subdomains x 11 outputs",
+            "nodes_per_step_per_gpu": nodes, "subdomains_per_node": 1 << 18, "outputs": 11,
             "gradients": "adjoint (reverse-mode interval)", "launch": "one persistent launch per step, CUDA graph",
-            "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"nodes sharded over {world} GPU(s)"}
+            "l2": "flushed between timed steps (256 MiB write); the kernel's state area (~0.3-0.9 GB) exceeds L2",
+            "parallelism": f"nodes sharded over {world} GPU(s)"}
 
 
 # --------------------------------------------------------------- clocks
@@ -154,21 +167,22 @@ def cpu_model() -> str:
 
 def oracle_rate(t, boxes, splits, seconds: float):
     """The oracle as it stands (fast exp/log mode, adjoint gradients, all host
-    cores) runs Steps 1-3 on whole workload nodes, as many as fit in about
-    `seconds`; then one core on 8192 subdomains of the first node. Returns
-    (subdomain-bounds/s, nodes, subdomains per node, cores, seconds,
-    subdomain-bounds/s on one core)."""
+    cores) runs Steps 1-2 on the first subdomains of the workload's first
+    node, as many as fit in about `seconds`; then one core on a tenth of that.
+    Returns (subdomain-bounds/s, subdomains, cores, seconds, subdomain-bounds/s
+    on one core)."""
     import oracle
     cores = oracle.max_threads()
-    S = int(np.prod(splits[0].astype(np.int64)))
     t0 = time.perf_counter()
-    oracle.bound_nodes(t, boxes[:1], splits[:1], grad_mode="adjoint", tight=False)
+    probe = 64 * cores
+    oracle.enclose(t, boxes[0], splits[0], first=0, count=probe, grad_mode="adjoint", tight=False)
     d1 = max(time.perf_counter() - t0, 1e-4)
-    k = int(min(len(boxes), max(1, round(seconds / d1))))
+    S = int(np.prod(splits[0].astype(np.int64)))
+    count = int(min(S, max(probe, probe * seconds / d1)))
     t0 = time.perf_counter()
-    oracle.bound_nodes(t, boxes[:k], splits[:k], grad_mode="adjoint", tight=False)
+    oracle.enclose(t, boxes[0], splits[0], first=0, count=count, grad_mode="adjoint", tight=False)
     dt = time.perf_counter() - t0
-    one = min(8192, S)
+    one = max(16, count // (10 * cores))
     oracle.set_threads(1)
     try:
         t0 = time.perf_counter()
@@ -176,29 +190,32 @@ def oracle_rate(t, boxes, splits, seconds: float):
         d_one = time.perf_counter() - t0
     finally:
         oracle.set_threads(cores)
-    return k * S * t.n_out / dt, k, S, cores, dt, one * t.n_out / d_one
+    return count * t.n_out / dt, count, cores, dt, one * t.n_out / d_one
 
 
 def run_reference(args, rank, world):
-    """--impl reference: the oracle on the host cores, same metric and workload;
-    each step bounds whole nodes (Steps 1-3), as many as fit its time share"""
+    """--impl reference: the oracle on the host cores, same metric and
+    workload; each step encloses a bounded sample of the step's subdomains
+    (the first ones of the first node), sized so that the whole run stays
+    within a few minutes"""
     if rank != 0:
         return 0
     wl, t, boxes, splits = workload(0, 1, args.nodes)
     per_step = max(2.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
     import oracle
-    _, k, S, cores, _, _ = oracle_rate(t, boxes, splits, per_step)
+    _, count, cores, _, _ = oracle_rate(t, boxes, splits, per_step)
     times = []
+    S = int(np.prod(splits[0].astype(np.int64)))
     for step in range(args.warmup + args.steps):
-        first = (step * k) % max(1, len(boxes) - k + 1)
+        first = (step * count) % max(1, S - count + 1)
         t0 = time.perf_counter()
-        oracle.bound_nodes(t, boxes[first:first + k], splits[first:first + k], grad_mode="adjoint", tight=False)
+        oracle.enclose(t, boxes[0], splits[0], first=first, count=count, grad_mode="adjoint", tight=False)
         if step >= args.warmup:
             times.append(time.perf_counter() - t0)
     total = sum(times)
-    value = k * S * t.n_out * len(times) / total
-    sample = (f"{k} whole nodes of {S} subdomains per step (Steps 1-3, adjoint gradients, fast exp/log mode); "
-              f"CPU: {cpu_model()}")
+    value = count * t.n_out * len(times) / total
+    sample = (f"{count} subdomains per step (Steps 1-2 on consecutive subdomains of the first node, adjoint "
+              f"gradients, fast exp/log mode); CPU: {cpu_model()}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -235,7 +252,10 @@ def main():
     n_nodes = boxes.shape[0]
     subs_step = int(np.prod(splits.astype(np.int64), axis=1).sum())
     units_step = subs_step * t.n_out
-    p = ivb.Problem(t, grad_mode="adjoint", batched=1, use_graph=1, autotune=1, specialize=args.specialize)
+    t0 = time.perf_counter()
+    p = ivb.Problem(t, grad_mode="adjoint", batched=1, use_graph=1, autotune=1, specialize=args.specialize,
+                    max_nodes=max(64, n_nodes))
+    create_s = time.perf_counter() - t0
     boxes_d = torch.from_numpy(boxes).to(dev)
     splits_d = torch.from_numpy(splits).to(dev)
     out = {"lb": torch.empty(n_nodes, dtype=torch.float64, device=dev),
@@ -244,7 +264,8 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    for _ in range(max(3, args.warmup)):
+    warmup = max(3, args.warmup)
+    for _ in range(warmup):
         p.bound_nodes_ex(boxes_d, splits_d, out=out)
     torch.cuda.synchronize(dev)
 
@@ -273,86 +294,51 @@ def main():
     value = units_all / t_max
 
     # ------------------------------------------------ e2e through host buffers
+    r = p.bound_nodes_ex(boxes, splits)
     e2e_times = []
-    for k in range(args.steps + 1):
+    for k in range(max(1, args.e2e_steps)):
         t0 = time.perf_counter()
         r = p.bound_nodes_ex(boxes, splits)
-        if k > 0:
-            e2e_times.append(time.perf_counter() - t0)
+        e2e_times.append(time.perf_counter() - t0)
     e2e_local = sum(e2e_times)
     e2e_max = shard.max_over_ranks(e2e_local, dev)
     e2e_value = shard.sum_over_ranks(units_step * len(e2e_times), dev) / e2e_max
     h2d = boxes.nbytes + splits.nbytes
     d2h = r["lb"].nbytes + r["infeasible"].nbytes + r["ub"].nbytes
 
-    # ------------------------------------------------ roofline (FP64 pipe, ALU bound)
-    names = ("dfma", "dadd", "dmul", "ddiv", "drcp", "dsqrt", "exp", "log",
-             "own_rcp", "own_div", "own_sqrt", "own_exp", "own_log", "emu_mul", "mixed_mul", "emu_add", "mixed_add")
-    rates = {k: ivb.ivb_fp64_probe(k) for k in names}
-    probe = rates["dfma"]   # measured DFMA lane-op/s: the unit of the per-primitive costs
-    # peak of the FP64 pipe from unit counts and clocks: 2 DFMA lanes per clock per SM on
-    # GB300 (ncu's dfma peak_sustained), times the SMs and the SM clock sampled during the steps
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    clock_mhz = clk.get("sm_mhz") or 2070.0
-    peak = 2.0 * sms * clock_mhz * 1e6
-    for k, extra in (("log", "dadd"), ("own_log", "dadd"), ("dsqrt", "dmul"), ("own_sqrt", "dmul")):
-        # these probes carry one extra round-to-nearest add / multiply per operation
-        rates[k] = 1.0 / max(1.0 / rates[k] - 1.0 / rates[extra], 1e-30)
-    # cost of each category in DFMA issue slots: the primitives the kernel runs
-    cost = {"addsub": probe / rates["dadd"], "mul": probe / rates["dmul"], "div": probe / rates["own_div"],
-            "rcp": probe / rates["own_rcp"], "sqrt": probe / rates["own_sqrt"], "exp": probe / rates["own_exp"],
-            "log": probe / rates["own_log"], "rn": probe / rates["dadd"]}
-    vendor = {"addsub": probe / rates["dadd"], "mul": probe / rates["dmul"], "div": probe / rates["ddiv"],
-              "rcp": probe / rates["drcp"], "sqrt": probe / rates["dsqrt"], "exp": probe / rates["exp"],
-              "log": probe / rates["log"], "rn": probe / rates["dadd"]}
-    counts = p.op_counts()
-    slots_per_sub = sum(counts[k] * cost[k] for k in counts)
-    vendor_slots = sum(counts[k] * vendor[k] for k in counts)
-    ops_per_sub = sum(counts.values())
     step_s = t_local / args.steps
-    achieved = slots_per_sub * subs_step / step_s
-    roofline = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
-                "unit": "G FP64 DFMA-slot/s", "frac": achieved / peak,
-                "traffic": traffic_for(subs_step, "specialised" if args.specialize else "interpreter"),
-                "peak_source": f"derived: {sms} SMs x 2 FP64 lanes/clock x {clock_mhz:.0f} MHz (SM clock sampled "
-                               f"during the steps) = {2 * peak / 1e12:.3f} FP64 TFLOP/s",
-                "measured_probe_peak": probe / 1e9, "frac_of_measured_probe": achieved / probe,
-                "probe_note": "ivb_fp64_probe: 8 independent DFMA chains per thread, 32 warps per SM; "
-                              "primitive costs are in units of this rate",
-                "work_per_subdomain": {"endpoint_ops": ops_per_sub, "dfma_slots": slots_per_sub,
-                                       "counts": counts,
-                                       "dfma_slots_with_cuda_intrinsics": vendor_slots},
-                "primitive_rates_glanes": {k: v / 1e9 for k, v in rates.items()},
-                "kernel_share_note": "step time includes the two tiny key/finalize kernels and the queue copy; "
-                                     "the bounding kernel's share is in profiles/"}
+    roofline = roofline_block(p, subs_step, step_s, clk, dev, probes=True)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "warmup": warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_desc(args.nodes, world), "roofline": roofline,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "steps": len(e2e_times)},
             "gpu_launches": int(launches), "clocks": clk,
             "subdomains_per_s": value / t.n_out, "tuning": p.get_tuning(),
-            "kernel": kernel_desc(p)}
+            "kernel": kernel_desc(p, create_s)}
 
     if rank == 0 and world == 1:
-        rate, k, S, cores, secs, rate1 = oracle_rate(t, boxes, splits, args.cpu_seconds)
+        rate, count, cores, secs, rate1 = oracle_rate(t, boxes, splits, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"Steps 1-3 on {k} whole nodes of {S} subdomains ({secs:.1f} s; "
-                                          "adjoint gradients, fast exp/log mode)",
+                                "sample": f"Steps 1-2 on the first {count} subdomains of the first node "
+                                          f"({secs:.1f} s; adjoint gradients, fast exp/log mode); the reduction "
+                                          "of Step 3 is a min over them",
                                 "value_1core": rate1, "cpu": cpu_model()}
-    if rank == 0 and world == 1 and args.specialize:
-        line["interpreter"] = interpreter_compare(t, boxes_d, splits_d, out, flush, stream, subs_step, step_s)
+        if p.get_specialization()["active"]:
+            line["interpreter"] = interpreter_compare(t, boxes_d, splits_d, out, flush, stream, subs_step, step_s)
+    p.destroy()
+    if rank == 0 and world == 1 and args.secondary:
+        line["config2"] = config2_step(dev, flush, stream)
     if rank == 0 and world == 1 and args.bnb:
-        line["bnb"] = bnb_compare(t, wl, args.bnb_time)
+        line["bnb"] = [bnb_compare(int(c), args.bnb_cap5 if c.strip() == "5" else args.bnb_cap)
+                       for c in args.bnb_configs.split(",") if c.strip()]
     if rank == 0 and world == 1 and args.oracle_bnb > 0:
         line["oracle_bnb"] = oracle_bnb_study(args.oracle_bnb)
-    if rank == 0 and world == 1 and args.bnb_configs:
-        line["bnb_configs"] = bnb_config_study([int(c) for c in args.bnb_configs.split(",")], args.bnb_config_cap)
     if rank == 0 and world == 1 and args.patterns:
         line["differentiation"] = differentiation_compare()
         line["batching"] = batching_compare()
-    p.destroy()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -360,24 +346,77 @@ def main():
     return 0
 
 
-def kernel_desc(p):
+def roofline_block(p, subs_step, step_s, clk, dev, probes=False):
+    """FP64-pipe roofline of the bounding kernel. `achieved` counts the
+    algorithmic work: the static count of outward-rounded endpoint operations
+    per subdomain (ivb_op_counts: the value, adjoint and Mean Value Form rules,
+    decode) times the subdomains of a step, over the step time (the bounding
+    kernel is > 99.9 % of a step: profiles/ has the launch list). `peak` is the
+    FP64 pipe from unit counts and the SM clock sampled during the steps:
+    2 FP64 lanes per clock per SM x SMs x clock. Beside it, the issue-slot view
+    (`pipe_busy_frac`): each category priced in DFMA issue slots at the
+    measured rates of the primitives the kernel runs."""
+    import torch
+    from paper_2507_20769_gb300 import ivb
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clock_mhz = clk.get("sm_mhz") or 2070.0
+    peak = 2.0 * sms * clock_mhz * 1e6
+    counts = p.op_counts()
+    ops_per_sub = sum(counts.values())
+    achieved = ops_per_sub * subs_step / step_s
+    seg = p.get_segmentation()
+    which = "segmented" if seg["chunks"] else ("specialised" if p.get_specialization()["active"] else "interpreter")
+    rf = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "G FP64 endpoint-op/s",
+          "frac": achieved / peak, "traffic": traffic_for(subs_step, which),
+          "peak_source": f"derived: {sms} SMs x 2 FP64 lanes/clock x {clock_mhz:.0f} MHz (SM clock sampled during "
+                         f"the steps) = {2 * peak / 1e12:.3f} FP64 TFLOP/s; MEASURED_PEAKS.json has no FP64 figure",
+          "work_per_subdomain": {"endpoint_ops": ops_per_sub, "counts": counts,
+                                 "recomputed_operations": seg["recomputed"]},
+          "kernel": which}
+    if probes:
+        names = ("dfma", "dadd", "dmul", "own_rcp", "own_div", "own_sqrt", "own_exp", "own_log")
+        rates = {k: ivb.ivb_fp64_probe(k) for k in names}
+        probe = rates["dfma"]
+        for k, extra in (("own_log", "dadd"), ("own_sqrt", "dmul")):
+            # these probes carry one extra round-to-nearest add / multiply per operation
+            rates[k] = 1.0 / max(1.0 / rates[k] - 1.0 / rates[extra], 1e-30)
+        cost = {"addsub": probe / rates["dadd"], "mul": probe / rates["dmul"], "div": probe / rates["own_div"],
+                "rcp": probe / rates["own_rcp"], "sqrt": probe / rates["own_sqrt"], "exp": probe / rates["own_exp"],
+                "log": probe / rates["own_log"], "rn": probe / rates["dadd"]}
+        slots = sum(counts[k] * cost[k] for k in counts)
+        rf["pipe_busy_frac"] = slots * subs_step / step_s / peak
+        rf["issue_slot_view"] = {"dfma_slots_per_subdomain": slots, "measured_dfma_probe_glanes": probe / 1e9,
+                                 "frac_of_measured_probe": slots * subs_step / step_s / probe,
+                                 "primitive_rates_glanes": {k: v / 1e9 for k, v in rates.items()}}
+    return rf
+
+
+def kernel_desc(p, create_s=None):
     s = p.get_specialization()
+    d = {"problem_create_seconds": round(create_s, 2)} if create_s is not None else {}
     if not s["active"]:
-        return {"bounding_kernel": "tape interpreter (ivb::k_bound)"}
-    return {"bounding_kernel": "tape-specialised (ivb_jit_bound, NVRTC sm_103a at problem creation)",
-            "registers": s["registers"], "local_bytes": s["local_bytes"],
-            "compile_seconds": round(s["compile_seconds"], 2)}
+        d["bounding_kernel"] = "tape interpreter (ivb::k_bound)"
+        return d
+    seg = p.get_segmentation()
+    d.update({"bounding_kernel": ("segmented " if seg["chunks"] else "") +
+              "tape-specialised (ivb_jit_bound, NVRTC sm_103a at problem creation)",
+              "registers": s["registers"], "local_bytes": s["local_bytes"],
+              "compile_seconds": round(s["compile_seconds"], 2)})
+    if seg["chunks"]:
+        d["segmentation"] = seg
+    return d
 
 
 def interpreter_compare(t, boxes_d, splits_d, out, flush, stream, subs_step, step_s):
     """the same step through the tape interpreter (bit-identical bounds), for context"""
     import torch
     from paper_2507_20769_gb300 import ivb
-    p = ivb.Problem(t, grad_mode="adjoint", batched=1, use_graph=1, autotune=1, specialize=0)
-    for _ in range(3):
+    p = ivb.Problem(t, grad_mode="adjoint", batched=1, use_graph=1, autotune=1, specialize=0,
+                    max_nodes=max(64, int(boxes_d.shape[0])))
+    for _ in range(2):
         p.bound_nodes_ex(boxes_d, splits_d, out=out)
     ms = []
-    for _ in range(3):
+    for _ in range(2):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -385,10 +424,47 @@ def interpreter_compare(t, boxes_d, splits_d, out, flush, stream, subs_step, ste
         b.record(stream)
         torch.cuda.synchronize()
         ms.append(a.elapsed_time(b))
+    tun = p.get_tuning()
     p.destroy()
     m = float(np.median(ms))
     return {"ms_per_step": m, "subdomains_per_s": subs_step / (m / 1e3),
-            "specialised_speedup": m / (1e3 * step_s)}
+            "specialised_speedup": m / (1e3 * step_s), "tuning": tun}
+
+
+def config2_step(dev, flush, stream, steps=5):
+    """configuration 2 (n=4, objective + 3 constraints of 60 entries, 64 nodes
+    x 16^4 subdomains per step), the workload of earlier measurements, with the
+    library's choice of kernel (one compact tape-specialised program here)"""
+    import torch
+    from paper_2507_20769_gb300 import ivb
+    from paper_2507_20769_gb300 import workloads as W
+    wl = W.config_workload(2)
+    t = wl.tape
+    boxes = W.bisection_frontier(t.root_box, 64, seed=2026)
+    splits = np.tile(wl.splits, (64, 1)).astype(np.int32)
+    subs = 64 * int(np.prod(wl.splits))
+    bd, sd = torch.from_numpy(boxes).to(dev), torch.from_numpy(splits).to(dev)
+    with ivb.Problem(t, grad_mode="adjoint", specialize=-1) as p:
+        for _ in range(3):
+            p.bound_nodes_ex(bd, sd)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            p.bound_nodes_ex(bd, sd)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        step_s = sum(ms) / len(ms) / 1e3
+        clk = {"sm_mhz": None}
+        rf = roofline_block(p, subs, step_s, clk, dev)
+        kd = kernel_desc(p)
+    return {"workload": "configuration 2: n=4, 1+3 outputs x 60-entry tapes, 64 nodes x 16^4 subdomains",
+            "value": subs * t.n_out / step_s, "unit": UNIT, "ms_per_step": 1e3 * step_s, "steps": steps,
+            "roofline": {k: rf[k] for k in ("achieved", "peak", "unit", "frac", "kernel", "traffic")},
+            "kernel": kd}
 
 
 # source files each bounding kernel is built from (the traffic record is valid
@@ -396,6 +472,7 @@ def interpreter_compare(t, boxes_d, splits_d, out, flush, stream, subs_step, ste
 KERNEL_SOURCES = {
     "interpreter": ("ivb_kernels.cu", "ivb_bound_common.cuh", "ivb_iv.cuh", "ivb_fp64x.cuh", "ivb_emu.cuh"),
     "specialised": ("ivb_jit.cpp", "ivb_bound_common.cuh", "ivb_iv.cuh", "ivb_fp64x.cuh", "ivb_emu.cuh"),
+    "segmented": ("ivb_jit_seg.cpp", "ivb_bound_common.cuh", "ivb_iv.cuh", "ivb_fp64x.cuh", "ivb_emu.cuh"),
 }
 
 
@@ -476,29 +553,41 @@ def batching_compare():
     return res
 
 
-def bnb_compare(t, wl, cap):
-    """B&B wall clock to relative gap 1e-3: adjoint + batched vs plain"""
+def bnb_compare(cfg, cap):
+    """B&B wall clock to the configuration's gap (Section 3 B&B with this
+    library's Subdomain Lower Bounding), time-capped, final bounds at the cap:
+      adjoint_batched: the paper's MVF, adjoint gradients, 32 parents per
+        iteration bounded in one persistent launch (CUDA graph), the library's
+        kernel choice;
+      plain_forward_one_node_per_launch: MVF with forward tangents, one node
+        per launch;
+      host_additions: adjoint + batched with MVF meet NIE, the filtered
+        objective, constraint propagation on the host (3 rounds) and CPU/GPU
+        overlap."""
     from paper_2507_20769_gb300 import ivb
-    res = {"gap_rel": wl.gap_rel, "time_cap_s": cap}
-    arms = (
-        # the paper's method on this path: adjoint gradients, batched nodes, CUDA graph
-        ("adjoint_batched", dict(grad_mode="adjoint", batched=1), dict(batch=32)),
-        # plus the host-side additions: constraint propagation of every child and
-        # the host overlapping the GPU (next batch enqueued before the last is absorbed),
-        # with the tape-specialised kernel
-        ("adjoint_batched_propagate_overlap_specialised", dict(grad_mode="adjoint", batched=1, specialize=1),
-         dict(batch=32, propagate=3, overlap=1)),
-        ("plain_forward_one_node_per_launch", dict(grad_mode="forward", batched=0), dict(batch=1)),
-    )
+    from paper_2507_20769_gb300 import workloads as W
+    wl = W.config_workload(cfg)
+    t = wl.tape
+    split = (dict(splits=wl.splits) if wl.splits is not None
+             else dict(target=1 << (18 if cfg == 5 else 15), strategy="adaptive"))
+    res = {"config": cfg, "gap_abs": wl.gap_abs, "gap_rel": wl.gap_rel, "time_cap_s": cap,
+           "split": {k: (v.tolist() if hasattr(v, "tolist") else v) for k, v in split.items()}}
+    arms = (("adjoint_batched", dict(grad_mode="adjoint", batched=1, specialize=-1), dict(batch=32)),
+            ("plain_forward_one_node_per_launch", dict(grad_mode="forward", batched=0, specialize=0), dict(batch=1)),
+            ("host_additions", dict(grad_mode="adjoint", batched=1, specialize=-1, form="mvf_nie", filter=1),
+             dict(batch=32, propagate=3, overlap=1)))
     for name, opts, bopts in arms:
         with ivb.Problem(t, **opts) as p:
-            r = p.bnb_solve(t.root_box, splits=wl.splits, eps_abs=0.0, eps_rel=wl.gap_rel, time_limit=cap, **bopts)
+            r = p.bnb_solve(t.root_box, eps_abs=wl.gap_abs, eps_rel=wl.gap_rel, time_limit=cap, **split, **bopts)
+            kind = kernel_desc(p).get("bounding_kernel")
         gap = r["ub"] - r["lb"]
         res[name] = {"seconds": r["seconds"], "converged": r["converged"], "nodes": r["nodes"],
-                     "lb": r["lb"], "ub": r["ub"], "gap": gap,
-                     "rel_gap": gap / max(abs(r["ub"]), 1e-300) if np.isfinite(gap) else None}
+                     "subdomains": r["subdomains"], "lb": r["lb"], "ub": r["ub"],
+                     "gap": gap if np.isfinite(gap) else None,
+                     "rel_gap": gap / abs(r["ub"]) if np.isfinite(gap) and r["ub"] != 0 else None,
+                     "kernel": kind}
     a, b = res["adjoint_batched"], res["plain_forward_one_node_per_launch"]
-    c = res["adjoint_batched_propagate_overlap_specialised"]
+    c = res["host_additions"]
     if a["converged"] and b["converged"]:
         res["speedup_time_to_gap"] = b["seconds"] / a["seconds"]
     if c["converged"] and b["converged"]:
@@ -516,41 +605,11 @@ def oracle_bnb_study(cap):
         wl = W.config_workload(cfg)
         r = oracle.bnb(wl.tape, splits=wl.splits, eps_abs=wl.gap_abs, eps_rel=wl.gap_rel, grad_mode="adjoint",
                        tight=False, time_limit=cap)
+        gap = r["ub"] - r["lb"]
         out.append({"config": cfg, "seconds": r["seconds"], "converged": r["converged"], "nodes": r["nodes"],
-                    "lb": r["lb"], "ub": r["ub"], "cores": oracle.max_threads(), "cpu": cpu_model()})
-    return out
-
-
-def bnb_config_study(configs, cap):
-    """B&B to each configuration's gap: adjoint + batched (32 parents per
-    iteration), then + constraint propagation, + CPU/GPU overlap, + the
-    tape-specialised kernel (not for configuration 5, whose tapes are too
-    large to compile quickly), and with MVF meet NIE and the filtered
-    objective. Configurations 3 and 5 split each node by the
-    adaptive picker (2^15 and 2^18 subdomains per node)."""
-    from paper_2507_20769_gb300 import ivb
-    from paper_2507_20769_gb300 import workloads as W
-    out = []
-    for cfg in configs:
-        wl = W.config_workload(cfg)
-        t = wl.tape
-        split = (dict(splits=wl.splits) if wl.splits is not None
-                 else dict(target=1 << (18 if cfg == 5 else 15), strategy="adaptive"))
-        arms = [("adjoint_batched", {}, {}), ("+propagate", {}, dict(propagate=3)),
-                ("+propagate+overlap", {}, dict(propagate=3, overlap=1))]
-        if cfg != 5:
-            arms.append(("+propagate+overlap+specialised", dict(specialize=1), dict(propagate=3, overlap=1)))
-        # the bound form: MVF intersected with the natural interval extension, filtered objective
-        arms.append(("+propagate+overlap+mvf_nie+filter", dict(form="mvf_nie", filter=1),
-                     dict(propagate=3, overlap=1)))
-        for name, popts, bopts in arms:
-            with ivb.Problem(t, grad_mode="adjoint", batched=1, **popts) as p:
-                r = p.bnb_solve(t.root_box, batch=32, eps_abs=wl.gap_abs, eps_rel=wl.gap_rel, time_limit=cap,
-                                **split, **bopts)
-            gap = r["ub"] - r["lb"]
-            out.append({"config": cfg, "arm": name, "seconds": r["seconds"], "converged": r["converged"],
-                        "nodes": r["nodes"], "lb": r["lb"], "ub": r["ub"],
-                        "rel_gap": gap / abs(r["ub"]) if np.isfinite(gap) and r["ub"] != 0 else None})
+                    "lb": r["lb"], "ub": r["ub"],
+                    "rel_gap": gap / abs(r["ub"]) if np.isfinite(gap) and r["ub"] != 0 else None,
+                    "cores": oracle.max_threads(), "cpu": cpu_model()})
     return out
 
 

@@ -150,6 +150,18 @@ typedef struct {
                                   slots per chunk (0 = default 320)         */
     int32_t seg_regs;          /* segmented kernel: register budget of every
                                   chunk function, 64..255 (0 = default 128) */
+    int32_t threads_per_subdomain; /* segmented kernel with an own program
+                                  per output: 1, 2 or 4 threads (in different
+                                  warps of a block) share one subdomain, each
+                                  running the programs of a group of its
+                                  outputs; 0 (default): chosen by the
+                                  autotuner among those compiled            */
+    int32_t seg_sync;          /* segmented kernel: 1 the warps of a thread
+                                  group wait for each other after every chunk
+                                  function (they then run the same code and
+                                  share the instruction cache), 0 they run
+                                  freely; -1 (default): chosen by the
+                                  autotuner                                  */
 } ivb_options;
 
 typedef struct ivb_problem ivb_problem;
@@ -269,7 +281,11 @@ typedef struct {
     int32_t batch;             /* nodes popped per iteration (>= 1)         */
     int32_t split_mode;        /* 0: fixed `splits`; 1 + IVB_SPLIT_*: picker */
     const int32_t* splits;     /* [n] fixed splits (split_mode 0), host     */
-    int64_t target;            /* subdomains per node for the picker        */
+    int64_t target;            /* subdomains per node for the picker; 0: per
+                                  iteration the smallest power of two >= 2^8
+                                  (at most 2^20) with which the iteration's
+                                  children cover four waves of the tuned
+                                  bounding launch                            */
     double eps_abs, eps_rel;   /* optimality tolerance                      */
     int64_t max_nodes;         /* limit on bounded nodes (0 = none)         */
     double time_limit;         /* seconds (0 = none)                        */
@@ -296,6 +312,8 @@ typedef struct {
     double seconds;            /* wall clock of the whole solve             */
     int32_t converged;         /* 1 if the tolerance was met                */
     int64_t open_nodes;
+    int64_t split_target;      /* subdomains per node the picker was given in
+                                  the last iteration (0: fixed splits)       */
 } ivb_bnb_result;
 
 void ivb_bnb_options_default(ivb_bnb_options* o);
@@ -328,6 +346,23 @@ ivb_status ivb_host_gradient(const ivb_tape* tape, const double* box, int32_t ou
  * block threads, blocks per SM, tile, frame in shared (0/1). */
 ivb_status ivb_get_tuning(ivb_problem* p, int32_t* block_threads, int32_t* blocks_per_sm,
                           int32_t* tile, int32_t* frame_in_shared);
+
+/* Launch configuration of the batched path after autotuning: the three
+ * knobs of the bounding launch and what the tuner timed. */
+typedef struct {
+    int32_t block_threads;         /* threads per block                          */
+    int32_t blocks_per_sm;         /* resident blocks per SM (grid = SMs x this) */
+    int32_t tile;                  /* subdomains a block grabs from the work
+                                      counter at a time (a multiple of the
+                                      subdomains per pass)                      */
+    int32_t frame_in_shared;       /* interpreter frames in shared memory (0/1)  */
+    int32_t threads_per_subdomain; /* threads sharing one subdomain's outputs    */
+    int32_t subdomains_per_pass;   /* block_threads / threads_per_subdomain      */
+    int32_t chunk_sync;            /* segmented kernel: groups kept on one chunk */
+    int32_t candidates;            /* launch configurations timed (0: none)      */
+    float best_ms, worst_ms;       /* their times on the tuning sample           */
+} ivb_tuning;
+ivb_status ivb_get_tuning_ex(ivb_problem* p, ivb_tuning* tuning);
 
 /* The tape-specialised kernel of a problem (each may be NULL): active (0/1),
  * registers per thread, local memory bytes per thread, NVRTC compile time in

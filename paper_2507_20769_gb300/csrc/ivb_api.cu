@@ -175,24 +175,26 @@ size_t smem_bytes(const ivb_problem* p, int block, int frame_smem) {
 }
 
 // the reduce-mode bounding kernel: tape-specialised when compiled, else the interpreter
-cudaError_t launch_reduce(ivb_problem* p, const KParams& K, int grid, int block, int frame_smem, cudaStream_t s) {
-    if (use_jit(p)) return jit_launch(p->jit, K, grid, block, s);
+cudaError_t launch_reduce(ivb_problem* p, const KParams& K, int grid, int block, int frame_smem, cudaStream_t s,
+                          int tpsub, bool sync) {
+    if (use_jit(p)) return jit_launch(p->jit, K, grid, block, s, tpsub, sync);
     return launch_bound(kernel_mode(p, false), K, grid, block, smem_bytes(p, block, frame_smem), s);
 }
 
 // resident blocks per SM of the reduce kernel
-int reduce_occupancy(ivb_problem* p, int block, int frame_smem) {
-    if (use_jit(p)) return block <= p->jit.max_threads ? jit_occupancy(p->jit, block) : 0;
+int reduce_occupancy(ivb_problem* p, int block, int frame_smem, int tpsub = 1, bool sync = false) {
+    if (use_jit(p)) return block <= p->jit.max_threads ? jit_occupancy(p->jit, block, tpsub, sync) : 0;
     return occupancy_blocks(kernel_mode(p, false), block, smem_bytes(p, block, frame_smem));
 }
 
 // enqueue: keys, counter, bound kernel, finalize (the batched graph body)
-ivb_status enqueue_bound(ivb_problem* p, int grid, int block, int tile, int frame_smem, int max_nodes, cudaStream_t s) {
+ivb_status enqueue_bound(ivb_problem* p, int grid, int block, int tile, int frame_smem, int max_nodes, cudaStream_t s,
+                         int tpsub, bool sync) {
     CK(launch_init_keys(p->d_keys, p->d_queue, max_nodes, p->n_out, s));
     CK(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned long long), s));
     KParams K = make_params(p, frame_smem);
     K.tile = tile;
-    CK(launch_reduce(p, K, grid, block, frame_smem, s));
+    CK(launch_reduce(p, K, grid, block, frame_smem, s, tpsub, sync));
     FinalizeParams F{};
     F.keys = p->d_keys;
     F.queue = p->d_queue;
@@ -212,33 +214,58 @@ ivb_status enqueue_bound(ivb_problem* p, int grid, int block, int tile, int fram
 }
 
 struct TuneCand {
-    int block, bps, smem;
+    int block, bps, smem, tpsub, tile_mult;
+    bool sync;
 };
 
-// Pick block size, blocks per SM and frame placement by timing the bound
-// kernel on the first subdomains of the staged batch (results do not depend on
-// the choice). The timed index range is capped at a few waves of the widest
-// candidate grid so that tuning stays a small fraction of one call.
+// threads-per-subdomain values the loaded kernel offers (1 unless segmented)
+std::vector<int> tpsub_choices(const ivb_problem* p) {
+    std::vector<int> v{1};
+    if (use_jit(p))
+        for (int t : {2, 4})
+            if (p->jit.kern_t[tpsub_index(t)] && (p->opt.threads_per_subdomain == 0 || p->opt.threads_per_subdomain == t))
+                v.push_back(t);
+    if (p->opt.threads_per_subdomain > 1 && v.size() > 1) v.erase(v.begin());   // a fixed T > 1 excludes 1
+    return v;
+}
+
+// chunk synchronisation choices: the segmented kernels come with and without
+std::vector<bool> sync_choices(const ivb_problem* p) {
+    if (!use_jit(p) || !p->jit.kern_sync[0]) return {false};
+    if (p->opt.seg_sync == 0) return {false};
+    if (p->opt.seg_sync == 1) return {true};
+    return {false, true};
+}
+
+// Pick block size, blocks per SM, frame placement, threads per subdomain and
+// subdomains per grab (tile) by timing the bound kernel on the first
+// subdomains of the staged batch (results do not depend on the choice). The
+// timed index range is capped at a few waves of the widest candidate grid so
+// that tuning stays a small fraction of one call. Stage 1 times every
+// (threads per subdomain, block, blocks per SM, frame placement); stage 2
+// times larger grabs (4 and 16 passes per grab) for the best of stage 1.
 ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
     std::vector<TuneCand> cands;
     const int blocks[] = {64, 128, 256};
     const int bpss[] = {1, 2, 3, 4, 6, 8};
     int max_threads = 0;
-    for (int b : blocks)
-        for (int k : bpss) {
-            const int warps = b * k / 32;
-            if (warps < 4 || warps > 32) continue;
-            for (int sm = 0; sm < 2; ++sm) {
-                const size_t bytes = smem_bytes(p, b, sm);
-                if (sm && (use_jit(p) || bytes + 1024 > (size_t)p->smem_optin || bytes * k > 220 * 1024)) continue;
-                if (p->opt.frame_in_shared == 0 && sm) continue;
-                if (p->opt.frame_in_shared == 1 && !sm && !use_jit(p)) continue;
-                if (reduce_occupancy(p, b, sm) < k) continue;
-                cands.push_back({b, k, sm});
-                max_threads = std::max(max_threads, b * k * p->sm_count);
+    for (bool sy : sync_choices(p))
+    for (int t : tpsub_choices(p))
+        for (int b : blocks)
+            for (int k : bpss) {
+                const int warps = b * k / 32;
+                if (warps < 4 || warps > 32 || b < 32 * t) continue;
+                for (int sm = 0; sm < 2; ++sm) {
+                    const size_t bytes = smem_bytes(p, b, sm);
+                    if (sm && (use_jit(p) || bytes + 1024 > (size_t)p->smem_optin || bytes * k > 220 * 1024)) continue;
+                    if (p->opt.frame_in_shared == 0 && sm) continue;
+                    if (p->opt.frame_in_shared == 1 && !sm && !use_jit(p)) continue;
+                    if (reduce_occupancy(p, b, sm, t, sy) < k) continue;
+                    cands.push_back({b, k, sm, t, 1, sy});
+                    max_threads = std::max(max_threads, b * k * p->sm_count);
+                }
             }
-        }
-    if (cands.empty()) cands.push_back({64, 1, 0});
+    if (cands.empty()) cands.push_back({64, 1, 0, 1, 1, false});
     // time only [0, cap) of the global index range
     const long long cap = std::min<long long>(total, std::max<long long>(4LL * max_threads, 1LL << 18));
     long long* hdr = reinterpret_cast<long long*>(p->h_queue);
@@ -249,24 +276,42 @@ ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    float best = 1e30f;
+    float best = 1e30f, worst = 0.f;
     TuneCand bc = cands[0];
     ivb_status st = IVB_OK;
-    for (const TuneCand& c : cands) {
+    int timed = 0;
+    auto time_one = [&](const TuneCand& c) -> ivb_status {
         const int grid = p->sm_count * c.bps;
-        if (reduce_units(p) > 0) st = ensure_frame(p, grid, c.block, reduce_units(p));
-        if (st) break;
-        const int tile = c.block;   // one pass per grab: the smallest tail at the end of a launch
-        for (int rep = 0; rep < 2 && !st; ++rep) {      // warm-up, then timed
-            if (rep == 1) { cudaError_t ce = cudaEventRecord(e0, s); if (ce) { st = cuda_fail(p, ce, "event"); break; } }
-            st = enqueue_bound(p, grid, c.block, tile, c.smem, p->max_nodes, s);
+        ivb_status r = IVB_OK;
+        if (reduce_units(p) > 0) r = ensure_frame(p, grid, c.block, reduce_units(p));
+        if (r) return r;
+        const int tile = c.tile_mult * (c.block / c.tpsub);
+        for (int rep = 0; rep < 2; ++rep) {      // warm-up, then timed
+            if (rep == 1) { cudaError_t ce = cudaEventRecord(e0, s); if (ce) return cuda_fail(p, ce, "event"); }
+            r = enqueue_bound(p, grid, c.block, tile, c.smem, p->max_nodes, s, c.tpsub, c.sync);
+            if (r) return r;
         }
-        if (st) break;
         CK(cudaEventRecord(e1, s));
         CK(cudaEventSynchronize(e1));
         float ms = 0;
         CK(cudaEventElapsedTime(&ms, e0, e1));
+        ++timed;
+        worst = std::max(worst, ms);
         if (ms < best) { best = ms; bc = c; }
+        return IVB_OK;
+    };
+    for (const TuneCand& c : cands) {
+        st = time_one(c);
+        if (st) break;
+    }
+    if (!st && p->opt.tile <= 0) {
+        const TuneCand base = bc;
+        for (int mult : {4, 16}) {
+            TuneCand c = base;
+            c.tile_mult = mult;
+            st = time_one(c);
+            if (st) break;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -278,7 +323,12 @@ ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
     p->block = bc.block;
     p->bps = bc.bps;
     p->frame_smem = bc.smem;
-    p->tile = bc.block;
+    p->tpsub = bc.tpsub;
+    p->chunk_sync = bc.sync;
+    p->tile = bc.tile_mult * (bc.block / bc.tpsub);
+    p->tune_candidates = timed;
+    p->tune_best_ms = best;
+    p->tune_worst_ms = worst;
     p->tuned = true;
     p->cfg_ready = true;
     if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
@@ -293,10 +343,14 @@ ivb_status default_tuning(ivb_problem* p) {
     else if (p->opt.frame_in_shared == 1) p->frame_smem = 1;
     else if (p->opt.frame_in_shared == 0) p->frame_smem = 0;
     else p->frame_smem = (bytes + 1024 <= (size_t)p->smem_optin && bytes * p->bps <= 220 * 1024) ? 1 : 0;
-    const int occ = reduce_occupancy(p, p->block, p->frame_smem);
+    p->tpsub = tpsub_choices(p).front();
+    if (p->block < 32 * p->tpsub) p->tpsub = 1;
+    p->chunk_sync = sync_choices(p).front();
+    const int occ = reduce_occupancy(p, p->block, p->frame_smem, p->tpsub, p->chunk_sync);
     if (occ < 1) return fail(p, IVB_ENOTSUP, "launch configuration does not fit on an SM");
     if (p->bps > occ) p->bps = occ;
-    p->tile = p->opt.tile > 0 ? ((p->opt.tile + p->block - 1) / p->block) * p->block : p->block;
+    const int per = p->block / p->tpsub;
+    p->tile = p->opt.tile > 0 ? ((p->opt.tile + per - 1) / per) * per : per;
     p->cfg_ready = true;
     const bool explicit_cfg = p->opt.block_threads > 0 || p->opt.blocks_per_sm > 0;
     if (!p->opt.autotune || explicit_cfg) p->tuned = true;
@@ -353,8 +407,18 @@ cudaError_t specialize_seg(ivb_problem* p, const std::vector<Ins>& ins, const st
     double secs = 0.0;
     *msg = jit_seg_compile(src, pol.max_regs, cubin, tables, &secs, nullptr, nullptr);
     if (!msg->empty()) return cudaSuccess;
-    const cudaError_t ce = jit_load(cubin, tables, p->jit);
+    cudaError_t ce = jit_load(cubin, tables, p->jit);
     if (ce != cudaSuccess) return ce;
+    p->jit.kern_t[0] = p->jit.kern;
+    for (int t : src.ts) {
+        const std::string name = "ivb_jit_bound_t" + std::to_string(t);
+        if (t > 1) {
+            ce = cudaLibraryGetKernel(&p->jit.kern_t[tpsub_index(t)], p->jit.lib, name.c_str());
+            if (ce != cudaSuccess) return ce;
+        }
+        ce = cudaLibraryGetKernel(&p->jit.kern_sync[tpsub_index(t)], p->jit.lib, (name + "_sync").c_str());
+        if (ce != cudaSuccess) return ce;
+    }
     p->jit.mode = KM_ADJ_REDUCE;
     p->jit.emulate = emu;
     p->jit.compact = true;
@@ -408,6 +472,8 @@ extern "C" void ivb_options_default(ivb_options* o) {
     o->recompute = -1;
     o->seg_chunk = 0;
     o->seg_regs = 0;
+    o->threads_per_subdomain = 0;
+    o->seg_sync = -1;
 }
 
 extern "C" ivb_status ivb_create_problem(const ivb_tape* tape, const ivb_options* opt, ivb_problem** out) {
@@ -429,6 +495,10 @@ extern "C" ivb_status ivb_create_problem(const ivb_tape* tape, const ivb_options
         return fail(nullptr, IVB_EINVAL, "specialize = 3 (segmented) needs grad_mode IVB_GRAD_ADJOINT");
     if (o.recompute < -1 || o.recompute > 2) return fail(nullptr, IVB_EINVAL, "recompute must be -1, 0, 1 or 2");
     if (o.seg_chunk < 0 || o.seg_chunk > 100000) return fail(nullptr, IVB_EINVAL, "seg_chunk must be in [0, 100000]");
+    if (o.threads_per_subdomain != 0 && o.threads_per_subdomain != 1 && o.threads_per_subdomain != 2 &&
+        o.threads_per_subdomain != 4)
+        return fail(nullptr, IVB_EINVAL, "threads_per_subdomain must be 0 (tuned), 1, 2 or 4");
+    if (o.seg_sync < -1 || o.seg_sync > 1) return fail(nullptr, IVB_EINVAL, "seg_sync must be -1, 0 or 1");
     if (o.seg_regs != 0 && (o.seg_regs < 64 || o.seg_regs > 255))
         return fail(nullptr, IVB_EINVAL, "seg_regs must be 0 or in [64, 255]");
     if (o.emulate < -1 || o.emulate > 15) return fail(nullptr, IVB_EINVAL, "emulate must be -1 or a bitmask in [0, 15]");
@@ -602,8 +672,8 @@ ivb_status bound_nodes_impl(ivb_problem* p, int32_t n_nodes, const double* boxes
             CK(launch_init_keys(p->d_keys, p->d_queue, 1, p->n_out, s));
             CK(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned long long), s));
             KParams K = make_params(p, p->frame_smem);
-            K.tile = p->block;
-            CK(launch_reduce(p, K, grid, p->block, p->frame_smem, s));
+            K.tile = p->block / p->tpsub;
+            CK(launch_reduce(p, K, grid, p->block, p->frame_smem, s, p->tpsub, p->chunk_sync));
             FinalizeParams F{};
             F.keys = p->d_keys; F.queue = p->d_queue; F.max_nodes = 1; F.n_out = p->n_out; F.obj = p->obj;
             F.filter = p->opt.filter; F.out_kind = p->d_out_kind;
@@ -632,7 +702,8 @@ ivb_status bound_nodes_impl(ivb_problem* p, int32_t n_nodes, const double* boxes
             if (!p->gexec) {
                 cudaGraph_t g = nullptr;
                 CK(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
-                st = enqueue_bound(p, grid, p->block, p->tile, p->frame_smem, p->max_nodes, p->cap_stream);
+                st = enqueue_bound(p, grid, p->block, p->tile, p->frame_smem, p->max_nodes, p->cap_stream, p->tpsub,
+                                   p->chunk_sync);
                 cudaGraph_t gg = nullptr;
                 cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &gg);
                 if (st) { if (gg) cudaGraphDestroy(gg); return st; }
@@ -646,7 +717,7 @@ ivb_status bound_nodes_impl(ivb_problem* p, int32_t n_nodes, const double* boxes
             CK(cudaGraphLaunch(p->gexec, s));
             p->launches += 3;
         } else {
-            st = enqueue_bound(p, grid, p->block, p->tile, p->frame_smem, p->max_nodes, s);
+            st = enqueue_bound(p, grid, p->block, p->tile, p->frame_smem, p->max_nodes, s, p->tpsub, p->chunk_sync);
             if (st) return st;
         }
     }
@@ -810,6 +881,21 @@ extern "C" ivb_status ivb_get_tuning(ivb_problem* p, int32_t* block_threads, int
     if (blocks_per_sm) *blocks_per_sm = p->bps;
     if (tile) *tile = p->tile;
     if (frame_in_shared) *frame_in_shared = p->frame_smem;
+    return IVB_OK;
+}
+
+extern "C" ivb_status ivb_get_tuning_ex(ivb_problem* p, ivb_tuning* t) {
+    if (!p || !t) return fail(p, IVB_EINVAL, "problem handle and result are required");
+    t->block_threads = p->block;
+    t->blocks_per_sm = p->bps;
+    t->tile = p->tile;
+    t->frame_in_shared = p->frame_smem;
+    t->threads_per_subdomain = p->tpsub;
+    t->chunk_sync = p->chunk_sync ? 1 : 0;
+    t->subdomains_per_pass = p->block / std::max(1, p->tpsub);
+    t->candidates = p->tune_candidates;
+    t->best_ms = p->tune_best_ms;
+    t->worst_ms = p->tune_worst_ms;
     return IVB_OK;
 }
 

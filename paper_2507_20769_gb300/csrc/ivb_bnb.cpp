@@ -111,9 +111,9 @@ extern "C" ivb_status ivb_bnb_solve(ivb_problem* p, int32_t n, const double* roo
         p->err = "ivb_bnb_solve: root, options and result are required and n must equal the problem's n_vars";
         return IVB_EINVAL;
     }
-    if (o->batch < 1 || (o->split_mode == 0 && !o->splits) || (o->split_mode > 0 && o->target < 1) ||
+    if (o->batch < 1 || (o->split_mode == 0 && !o->splits) || (o->split_mode > 0 && o->target < 0) ||
         o->propagate < 0) {
-        p->err = "ivb_bnb_solve: batch >= 1, splits (split_mode 0) or target >= 1, propagate >= 0";
+        p->err = "ivb_bnb_solve: batch >= 1, splits (split_mode 0) or target >= 0, propagate >= 0";
         return IVB_EINVAL;
     }
     cudaStream_t stream = (cudaStream_t)stream_;
@@ -164,13 +164,25 @@ extern "C" ivb_status ivb_bnb_solve(ivb_problem* p, int32_t n, const double* roo
         return o->propagate == 0 || ivb::host_propagate(H, k->box.data(), UB, o->propagate) == 0;
     };
     // stage and enqueue a batch; its results arrive in the pinned buffers
+    int64_t last_target = o->split_mode > 0 ? o->target : 0;
     auto launch = [&](Batch& b) -> ivb_status {
         const int cnt = (int)b.kids.size();
+        // subdomains per child for the split picker: the given target, or with
+        // target 0 the smallest power of two >= 2^8 (at most 2^20) with which
+        // this iteration's children cover four waves of the bounding launch
+        int64_t target = o->target;
+        if (o->split_mode > 0 && target == 0) {
+            const int64_t wave = (int64_t)p->sm_count * std::max(1, p->bps) * (std::max(1, p->block) / std::max(1, p->tpsub));
+            const int64_t want = (4 * wave + cnt - 1) / std::max(1, cnt);
+            target = 1 << 8;
+            while (target < want && target < (1 << 20)) target <<= 1;
+        }
+        last_target = target;
         for (int k = 0; k < cnt; ++k) {
             std::memcpy(&b.boxes[(size_t)k * n * 2], b.kids[k]->box.data(), n * 2 * sizeof(double));
             int32_t* sp = &b.splits[(size_t)k * n];
             if (o->split_mode == 0) std::memcpy(sp, o->splits, n * sizeof(int32_t));
-            else if (ivb_status e = ivb_pick_splits(n, b.kids[k]->box.data(), ref.data(), o->target,
+            else if (ivb_status e = ivb_pick_splits(n, b.kids[k]->box.data(), ref.data(), target,
                                                     o->split_mode - 1, sp))
                 return e;
             int64_t s = 1;
@@ -297,6 +309,7 @@ extern "C" ivb_status ivb_bnb_solve(ivb_problem* p, int32_t n, const double* roo
     res->seconds = elapsed();
     res->converged = converged;
     res->open_nodes = (int64_t)heap.size();
+    res->split_target = last_target;
     release();
     return st;
 }

@@ -77,8 +77,11 @@ struct Sub {
 // Blocks grab tiles of the global subdomain index space from a device counter
 // and map indices to nodes through the queue's prefix sums; body(sub) runs
 // for every lane of every pass (idle lanes included, for the warp reductions).
+// `per` subdomains per pass: thread t takes subdomain g0 + t % per, so with
+// per = blockDim / T the T groups of blockDim / T threads (whole warps) take
+// the same subdomains (T threads per subdomain); per = blockDim otherwise.
 template <class Body>
-__device__ __forceinline__ void tile_loop(const KParams& P, Body&& body) {
+__device__ __forceinline__ void tile_loop_per(const KParams& P, const int per, Body&& body) {
     const long long* qh = reinterpret_cast<const long long*>(P.queue);
     const int n_nodes = (int)qh[0];
     const long long total = qh[1];
@@ -92,9 +95,9 @@ __device__ __forceinline__ void tile_loop(const KParams& P, Body&& body) {
         const long long base = s_base;
         if (base >= total) break;
         const long long end = base + P.tile < total ? base + P.tile : total;
-        for (long long g0 = base; g0 < end; g0 += blockDim.x) {
+        for (long long g0 = base; g0 < end; g0 += per) {
             Sub s;
-            s.g = g0 + threadIdx.x;
+            s.g = g0 + (int)(threadIdx.x % (unsigned)per);
             s.valid = s.g < end;
             // node of g: largest node with off[node] <= g
             s.node = -1;
@@ -115,6 +118,11 @@ __device__ __forceinline__ void tile_loop(const KParams& P, Body&& body) {
             body(s);
         }
     }
+}
+
+template <class Body>
+__device__ __forceinline__ void tile_loop(const KParams& P, Body&& body) {
+    tile_loop_per(P, (int)blockDim.x, body);
 }
 
 // Step 1 for dimension i (Section 2.2 splitting item i): j = kk mod N_i, then

@@ -493,15 +493,28 @@ cudaError_t jit_load(const std::vector<char>& cubin, const std::string& tables_n
     return cudaSuccess;
 }
 
-cudaError_t jit_launch(const JitKernel& K, const KParams& P, int grid, int block, cudaStream_t s) {
-    KParams p = P;
-    void* args[] = {&p};
-    return cudaLaunchKernel((const void*)K.kern, dim3(grid), dim3(block), args, 0, s);
+static cudaKernel_t pick(const JitKernel& K, int tpsub, bool sync) {
+    const int i = tpsub_index(tpsub);
+    if (i < 0) return nullptr;
+    if (sync) return K.kern_sync[i];
+    if (i > 0) return K.kern_t[i];
+    return K.kern;
 }
 
-int jit_occupancy(const JitKernel& K, int block) {
+cudaError_t jit_launch(const JitKernel& K, const KParams& P, int grid, int block, cudaStream_t s, int tpsub,
+                       bool sync) {
+    const cudaKernel_t k = pick(K, tpsub, sync);
+    if (!k) return cudaErrorInvalidValue;
+    KParams p = P;
+    void* args[] = {&p};
+    return cudaLaunchKernel((const void*)k, dim3(grid), dim3(block), args, 0, s);
+}
+
+int jit_occupancy(const JitKernel& K, int block, int tpsub, bool sync) {
+    const cudaKernel_t k = pick(K, tpsub, sync);
+    if (!k) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)K.kern, block, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)k, block, 0) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }

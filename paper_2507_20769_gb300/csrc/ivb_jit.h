@@ -45,6 +45,11 @@ struct JitKernel {
     // recomputed forward operations per subdomain, recomputation policy
     int state_units = 0, chunks = 0, recompute = -1;
     long long state_loads = 0, state_stores = 0, recomputed = 0;
+    // kernels of the segmented variant for 1, 2 and 4 threads per subdomain
+    // (index 0, 1, 2; nullptr where not compiled), without and with the
+    // warps of a thread group kept on the same chunk by a barrier
+    cudaKernel_t kern_t[3] = {nullptr, nullptr, nullptr};
+    cudaKernel_t kern_sync[3] = {nullptr, nullptr, nullptr};
 };
 
 // Segmented kernels for large tapes (ivb_jit_seg.cpp): the per-subdomain
@@ -61,10 +66,12 @@ struct SegPolicy {
     int max_regs = 128;          // register budget of every chunk function
 };
 struct SegSource {
-    std::string kernel;               // tile loop, Step 1, chunk calls, Step 3
+    std::string kernel;               // tile loop, Step 1, chunk calls, Step 3 (one kernel per T)
     std::vector<std::string> units;   // the chunk functions
+    std::vector<int> ts;              // threads per subdomain with a kernel: ivb_jit_bound (1), _t2, _t4
     int state_units = 0, chunks = 0;
     long long loads = 0, stores = 0, recomputed = 0;
+    std::string error;                // "" unless the program could not be planned
 };
 SegSource jit_seg_source(const HostProgram& P, const std::vector<Ins>& ins, const std::vector<RIns>& rins,
                          const std::vector<double>& consts, int block_max, int min_blocks, int emulate, int form,
@@ -83,8 +90,13 @@ std::string jit_source(const HostProgram& P, const std::vector<Ins>& ins, const 
 std::string jit_compile(const std::string& src, std::vector<char>& cubin, std::string& tables_name, double* seconds,
                         int* registers, int* spill_bytes);
 cudaError_t jit_load(const std::vector<char>& cubin, const std::string& tables_name, JitKernel& K);
-cudaError_t jit_launch(const JitKernel& K, const KParams& P, int grid, int block, cudaStream_t s);
-int jit_occupancy(const JitKernel& K, int block);
+// launch / occupancy of the kernel for `tpsub` threads per subdomain (1 for
+// every variant but the segmented one)
+cudaError_t jit_launch(const JitKernel& K, const KParams& P, int grid, int block, cudaStream_t s, int tpsub = 1,
+                       bool sync = false);
+int jit_occupancy(const JitKernel& K, int block, int tpsub = 1, bool sync = false);
+// index of a threads-per-subdomain value in JitKernel::kern_t (-1 if none)
+inline int tpsub_index(int t) { return t == 1 ? 0 : t == 2 ? 1 : t == 4 ? 2 : -1; }
 void jit_unload(JitKernel& K);
 
 }  // namespace ivb

@@ -106,7 +106,6 @@ struct Builder {
     std::vector<std::string> vname;
     std::vector<int> vtype;
     std::map<std::string, int> vid;
-    std::vector<Stmt> st;
 
     int var(const std::string& nm, int type = V_IV) {
         auto it = vid.find(nm);
@@ -129,7 +128,7 @@ struct Builder {
             return nm;
         }
         if (kind == K_VAR) {
-            if (role == 'p') {
+            if (role == 'p' || role == 'q') {
                 reads.push_back(var("c" + S(idx), V_DBL));
                 return "mk(c" + S(idx) + ", c" + S(idx) + ")";
             }
@@ -250,50 +249,80 @@ struct Builder {
         return s;
     }
 
-    // the whole per-subdomain program, in the order the compact kernel runs it
+    // One program per output (and, when the outputs' cones share entries, a
+    // point-sweep program for all of them first). An output's program runs
+    // the point sweep of its cone on [c,c] (unless shared), the forward sweep
+    // on X_k, the reverse sweep and the Mean Value Form; programs read X, c
+    // (and a shared point value) and leave F_o and f(c)_o in fixed slots, so
+    // any grouping of outputs over threads runs the same programs.
+    struct Prog {
+        std::vector<Stmt> st;
+        int out = -1;          // -1: the shared point sweep
+        double cost = 0.0;
+    };
+    std::vector<Prog> progs;
+    bool shared_point = false;
+
+    Stmt copy_stmt(const std::string& dst, char role, uint32_t kind, uint32_t ref, int o, int phase) {
+        Stmt s;
+        s.out = o;
+        s.phase = phase;
+        const std::string v = val(role, kind, ref, s.reads);
+        s.writes.push_back(var(dst));
+        s.code = dst + " = " + v + ";";
+        return s;
+    }
+
     void build() {
-        // point sweep on [c,c] over every output's cone
-        for (int i = P.pt_begin; i < P.pt_begin + P.pt_count; ++i) st.push_back(value_stmt('p', ins[i]));
-        for (int o = 0; o < no; ++o) {
-            Stmt s;
-            const std::string ref = val('p', (uint32_t)P.pt_out_kind[o], (uint32_t)P.pt_out_ref[o], s.reads);
-            s.writes.push_back(var("fc" + S(o)));
-            s.code = "fc" + S(o) + " = " + ref + ";";
-            st.push_back(s);
+        long long cone_sum = 0;
+        for (int o = 0; o < no; ++o) cone_sum += P.adj[o].fw_count;
+        // outputs whose cones overlap share one point sweep (no output groups)
+        shared_point = cone_sum > P.pt_count + P.pt_count / 8 + 16;
+        if (shared_point) {
+            Prog pp;
+            for (int i = P.pt_begin; i < P.pt_begin + P.pt_count; ++i) pp.st.push_back(value_stmt('p', ins[i]));
+            for (int o = 0; o < no; ++o)
+                pp.st.push_back(copy_stmt("fc" + S(o), 'p', (uint32_t)P.pt_out_kind[o], (uint32_t)P.pt_out_ref[o], -1, 0));
+            progs.push_back(pp);
         }
         for (int o = 0; o < no; ++o) {
+            Prog pr;
+            pr.out = o;
+            std::vector<Stmt>& q = pr.st;
             const AdjProgram& A = P.adj[o];
+            if (!shared_point) {
+                // the point sweep of this output's cone: its forward program on [c,c]
+                for (int i = A.fw_begin; i < A.fw_begin + A.fw_count; ++i) {
+                    Stmt t = value_stmt('q', ins[i]);
+                    t.out = o;
+                    t.phase = 0;
+                    q.push_back(t);
+                }
+                q.push_back(copy_stmt("fc" + S(o), 'q', (uint32_t)A.out_kind_ref, (uint32_t)A.out_ref, o, 0));
+            }
             for (int i = A.fw_begin; i < A.fw_begin + A.fw_count; ++i) {
-                Stmt s = value_stmt('r', ins[i]);
-                s.out = o;
-                st.push_back(s);
+                Stmt t = value_stmt('r', ins[i]);
+                t.out = o;
+                q.push_back(t);
             }
-            {
-                Stmt s;
-                s.out = o;
-                s.phase = 1;
-                const std::string ref = val('r', (uint32_t)A.out_kind_ref, (uint32_t)A.out_ref, s.reads);
-                s.writes.push_back(var("nie" + S(o)));
-                s.code = "nie" + S(o) + " = " + ref + ";";
-                st.push_back(s);
-            }
+            q.push_back(copy_stmt("nie" + S(o), 'r', (uint32_t)A.out_kind_ref, (uint32_t)A.out_ref, o, 1));
             if (!nie_only) {
-                Stmt s;
-                s.out = o;
-                s.phase = 2;
+                Stmt t;
+                t.out = o;
+                t.phase = 2;
                 for (int i = 0; i < n; ++i) {
-                    s.writes.push_back(var("g" + S(i)));
-                    s.code += "g" + S(i) + " = zero(); ";
+                    t.writes.push_back(var("g" + S(i)));
+                    t.code += "g" + S(i) + " = zero(); ";
                 }
                 if (A.out_wslot >= 0) {
-                    s.writes.push_back(var("w" + S(A.out_wslot)));
-                    s.code += "w" + S(A.out_wslot) + " = one();";
+                    t.writes.push_back(var("w" + S(A.out_wslot)));
+                    t.code += "w" + S(A.out_wslot) + " = one();";
                 }
-                st.push_back(s);
+                q.push_back(t);
                 for (int i = A.rv_begin; i < A.rv_begin + A.rv_count; ++i) {
                     Stmt r = reverse_stmt(rins[i]);
                     r.out = o;
-                    st.push_back(r);
+                    q.push_back(r);
                 }
             }
             // Mean Value Form (Definition 5), left to right, and the form
@@ -318,8 +347,11 @@ struct Builder {
                 m.cost = 2.0 * n + 2.0;
             }
             m.writes.push_back(var(F));
-            st.push_back(m);
+            q.push_back(m);
+            progs.push_back(pr);
         }
+        for (Prog& pr : progs)
+            for (const Stmt& t : pr.st) pr.cost += t.cost;
     }
 };
 
@@ -328,23 +360,23 @@ struct Chunk {
 };
 
 struct Plan {
-    std::vector<Chunk> chunks;
-    std::vector<std::set<int>> live_in;    // per chunk: read before written
-    std::vector<std::set<int>> live_out;   // per chunk: written or passed through and read later
-    std::vector<std::map<int, int>> slot_after;   // per boundary (after chunk c): var -> state slot
-    std::map<int, int> slot_pre;                  // after the prologue
+    std::vector<Chunk> chunks;                  // every program's chunks, program after program
+    std::vector<std::map<int, int>> load_slot;  // per chunk: variable read before written -> slot
+    std::vector<std::map<int, int>> store_slot; // per chunk: variable it hands on -> slot
+    std::vector<int> prog_first, prog_count;    // chunks of each program
     int n_slots = 0;
-    long long loads = 0, stores = 0, recomputed = 0;   // per subdomain
+    long long loads = 0, stores = 0, recomputed = 0;   // per subdomain (all programs)
 };
 
 // Cut the statement list into chunks of bounded estimated work and statement
 // count, then insert the recomputation of each reverse chunk's own forward
 // values according to the policy.
-std::vector<Chunk> cut(const Builder& B, double budget, int max_stmts, int policy, long long* recomputed) {
+std::vector<Chunk> cut(const Builder& B, const std::vector<Stmt>& prog, double budget, int max_stmts, int policy,
+                       long long* recomputed) {
     std::vector<Chunk> ch;
     Chunk cur;
     double cost = 0.0;
-    for (const Stmt& s : B.st) {
+    for (const Stmt& s : prog) {
         if (!cur.body.empty() && (cost + s.cost > budget || (int)cur.body.size() >= max_stmts)) {
             ch.push_back(cur);
             cur = Chunk{};
@@ -358,7 +390,7 @@ std::vector<Chunk> cut(const Builder& B, double budget, int max_stmts, int polic
     if (policy <= 0) return ch;
     // forward statement of each record, per output
     std::vector<std::map<int, const Stmt*>> fwd(B.no);
-    for (const Stmt& s : B.st)
+    for (const Stmt& s : prog)
         if (s.fk >= 0) fwd[s.out][s.fk] = &s;
     for (Chunk& c : ch) {
         std::vector<Stmt> out;
@@ -424,68 +456,70 @@ std::vector<Chunk> cut(const Builder& B, double budget, int max_stmts, int polic
     return ch;
 }
 
-// liveness over chunks and state slots for the values that cross boundaries
-void plan_state(const Builder& B, Plan& pl, const std::vector<int>& pro_writes, const std::vector<int>& epi_reads) {
-    const int C = (int)pl.chunks.size();
-    std::vector<std::set<int>> use(C), def(C);
+// Liveness over one program's chunks and state slots for the values that
+// cross chunk boundaries. Variables with a fixed slot (X_i, c_i, f(c)_o, F_o)
+// always live there; the others take working slots from `w0` on, released
+// one chunk after their last read (inside a chunk a live-in may be loaded
+// after another variable's store).
+std::string plan_prog(const Builder& B, const std::vector<Chunk>& ch, const std::map<int, int>& fixed,
+                      const std::set<int>& ends, int w0, Plan& pl) {
+    const int C = (int)ch.size();
+    std::vector<std::set<int>> use(C), def(C), live_out(C);
     for (int c = 0; c < C; ++c)
-        for (const Stmt& s : pl.chunks[c].body) {
-            for (int v : s.reads) if (!def[c].count(v)) use[c].insert(v);
-            for (int v : s.writes) def[c].insert(v);
+        for (const Stmt& t : ch[c].body) {
+            for (int v : t.reads) if (!def[c].count(v)) use[c].insert(v);
+            for (int v : t.writes) def[c].insert(v);
         }
-    pl.live_in.assign(C, {});
-    pl.live_out.assign(C, {});
-    std::set<int> live(epi_reads.begin(), epi_reads.end());
+    std::set<int> live = ends;
     for (int c = C - 1; c >= 0; --c) {
-        pl.live_out[c] = live;
+        live_out[c] = live;
         std::set<int> in = use[c];
         for (int v : live) if (!def[c].count(v)) in.insert(v);
-        pl.live_in[c] = in;
         live = in;
     }
-    // slots: the prologue writes pro_writes; those live into chunk 0 get slots.
-    // A slot released in chunk c (its variable is last read there) is reused
-    // from chunk c + 1 on: inside chunk c a live-in may be loaded after another
-    // variable's store.
+    for (int v : live)
+        if (!fixed.count(v)) return "internal: " + B.vname[v] + " is read before any statement writes it";
     std::vector<int> free_slots, released;
-    int next = 0;
-    auto get = [&]() { if (!free_slots.empty()) { int s = free_slots.back(); free_slots.pop_back(); return s; } return next++; };
-    std::map<int, int> cur;
-    for (int v : pro_writes) if (live.count(v)) cur[v] = get();
-    pl.slot_pre = cur;
-    pl.slot_after.assign(C, {});
+    int next = w0;
+    auto get = [&]() { if (!free_slots.empty()) { int q = free_slots.back(); free_slots.pop_back(); return q; } return next++; };
+    std::map<int, int> cur;   // working variable -> slot, live at the current boundary
     for (int c = 0; c < C; ++c) {
         free_slots.insert(free_slots.end(), released.begin(), released.end());
         released.clear();
+        std::map<int, int> ld, stv;
+        for (int v : use[c]) {
+            auto f = fixed.find(v);
+            ld[v] = f != fixed.end() ? f->second : cur.at(v);
+        }
         std::map<int, int> nxt;
         for (auto& kv : cur) {
-            if (pl.live_out[c].count(kv.first)) {
-                nxt[kv.first] = kv.second;     // passes through, or is redefined in place
-                if (def[c].count(kv.first)) pl.stores += 1;
-            } else {
-                released.push_back(kv.second);
-            }
+            if (live_out[c].count(kv.first)) nxt[kv.first] = kv.second;
+            else released.push_back(kv.second);
         }
-        for (int v : pl.live_out[c])
-            if (!nxt.count(v)) {
-                nxt[v] = get();
-                pl.stores += 1;
-            }
-        pl.loads += (long long)use[c].size();
+        for (int v : live_out[c]) {
+            if (!def[c].count(v)) continue;
+            auto f = fixed.find(v);
+            if (f != fixed.end()) { stv[v] = f->second; continue; }
+            if (!nxt.count(v)) nxt[v] = get();
+            stv[v] = nxt[v];
+        }
+        pl.loads += (long long)ld.size();
+        pl.stores += (long long)stv.size();
+        pl.load_slot.push_back(ld);
+        pl.store_slot.push_back(stv);
         cur = nxt;
-        pl.slot_after[c] = cur;
     }
-    pl.n_slots = next;
+    if (next > pl.n_slots) pl.n_slots = next;
+    return "";
 }
 
 // C++ of one chunk function
 std::string chunk_fn(const Builder& B, const Plan& pl, int c) {
     const Chunk& ch = pl.chunks[c];
-    const std::map<int, int>& in_slots = c == 0 ? pl.slot_pre : pl.slot_after[c - 1];
-    const std::map<int, int>& out_slots = pl.slot_after[c];
+    const std::map<int, int>& ld = pl.load_slot[c];
+    const std::map<int, int>& stv = pl.store_slot[c];
     std::string s = "extern \"C\" __device__ __noinline__ void ivb_ck" + S(c) +
                     "(double* __restrict__ st, const int ss) {\n  using namespace ivb;\n";
-    // declarations of every variable the chunk touches
     std::set<int> touched;
     for (const Stmt& t : ch.body) {
         for (int v : t.reads) touched.insert(v);
@@ -500,33 +534,27 @@ std::string chunk_fn(const Builder& B, const Plan& pl, int c) {
         if (!dv.empty()) s += dv + ";\n";
         if (!dd.empty()) s += dd + ";\n";
     }
-    // last write of each variable that leaves the chunk: store right after it
     std::map<int, size_t> last_write;
     for (size_t i = 0; i < ch.body.size(); ++i)
         for (int v : ch.body[i].writes) last_write[v] = i;
-    std::set<int> loaded;
-    auto load = [&](int v) -> std::string {
-        const int slot = in_slots.at(v);
-        if (B.vtype[v] == V_DBL) return "  " + B.vname[v] + " = st_d(st, ss, " + S(slot) + ");\n";
-        return "  " + B.vname[v] + " = st_ld(st, ss, " + S(slot) + ");\n";
-    };
-    std::set<int> written;
+    std::set<int> loaded, written;
     for (size_t i = 0; i < ch.body.size(); ++i) {
         const Stmt& t = ch.body[i];
         // live-ins are loaded before their first read (the scheduler hoists them)
         for (int v : t.reads)
             if (!written.count(v) && !loaded.count(v)) {
-                s += load(v);
+                const int slot = ld.at(v);
+                s += "  " + B.vname[v] + (B.vtype[v] == V_DBL ? " = st_d(st, ss, " : " = st_ld(st, ss, ") + S(slot) + ");\n";
                 loaded.insert(v);
             }
         s += "  " + t.code + "\n";
         for (int v : t.writes) written.insert(v);
-        for (int v : t.writes)
-            if (last_write[v] == i && out_slots.count(v) && pl.live_out[c].count(v)) {
-                const int slot = out_slots.at(v);
-                if (B.vtype[v] == V_DBL) s += "  st_sd(st, ss, " + S(slot) + ", " + B.vname[v] + ");\n";
-                else s += "  st_st(st, ss, " + S(slot) + ", " + B.vname[v] + ");\n";
-            }
+        for (int v : t.writes) {
+            auto it = stv.find(v);
+            if (last_write[v] == i && it != stv.end())
+                s += std::string(B.vtype[v] == V_DBL ? "  st_sd(st, ss, " : "  st_st(st, ss, ") + S(it->second) + ", " +
+                     B.vname[v] + ");\n";
+        }
     }
     s += "}\n";
     return s;
@@ -557,55 +585,122 @@ std::string unit_head(int emulate, bool kernel_unit) {
     return s;
 }
 
-// the kernel unit: tile loop, Step 1, the chunk calls, tests and Step 3
-std::string kernel_unit(const Builder& B, const Plan& pl, int block_max, int min_blocks, int emulate) {
-    std::string s = unit_head(emulate, true);
-    for (size_t c = 0; c < pl.chunks.size(); ++c)
-        s += "extern \"C\" __device__ void ivb_ck" + S(c) + "(double* __restrict__ st, const int ss);\n";
-    const int n = B.n, no = B.no;
-    s += "extern \"C\" __global__ void __launch_bounds__(" + S(block_max) + ", " + S(min_blocks) +
-         ") ivb_jit_bound(const ivb::KParams P) {\n";
+// fixed state slots: X_i at i, c_i at n + i, F_o at 2n + 2o, f(c)_o at 2n + 2o + 1
+int slot_X(int n, int i) { return i; }
+int slot_c(int n, int i) { return n + i; }
+int slot_F(int n, int o) { return 2 * n + 2 * o; }
+int slot_fc(int n, int o) { return 2 * n + 2 * o + 1; }
+
+// One kernel per number T of threads sharing a subdomain: a block's threads
+// form T groups of blockDim/T (whole warps); group g runs the programs of its
+// outputs on the same blockDim/T subdomains as the other groups. The tests
+// that need every output of a subdomain (a constraint proving it infeasible
+// for the filtered objective; the certified-feasible centre of the upper
+// bound) are combined through shared memory by the objective's group; each
+// group reduces its own outputs' hulls. T = 1 is the plain kernel.
+std::string kernel_fn(const Builder& B, const Plan& pl, const std::vector<std::vector<int>>& groups, int T,
+                      bool sync, const std::string& name, int block_max, int min_blocks) {
+    const int n = B.n, no = B.no, obj = B.P.obj;
+    int gobj = 0;
+    for (int g = 0; g < T; ++g)
+        for (int o : groups[g]) if (o == obj) gobj = g;
+    std::string s = "extern \"C\" __global__ void __launch_bounds__(" + S(block_max) + ", " + S(min_blocks) + ") " +
+                    name + "(const ivb::KParams P) {\n";
     s += "  using namespace ivb;\n";
     s += "  double* const st = P.gframe + (size_t)blockIdx.x * P.frame_units * blockDim.x + threadIdx.x;\n";
     s += "  const int ss = blockDim.x;\n";
-    s += "  tile_loop(P, [&](const Sub& s) {\n";
+    s += "  const int per = blockDim.x / " + S(T) + ";\n";
+    s += "  const int grp = threadIdx.x / per;\n";
+    if (T > 1) s += "  __shared__ unsigned char s_fl[" + S(block_max) + "];\n";
+    s += "  tile_loop_per(P, per, [&](const Sub& s) {\n";
     {
         std::string f = "    iv ";
         for (int o = 0; o < no; ++o) f += (o ? ", F" : "F") + S(o) + " = zero()";
         s += f + ";\n";
     }
-    s += "    bool cert = false;\n";
+    s += "    unsigned int fl = 0u;   // 1: an output proves the subdomain infeasible; 2: the centre is not certified feasible\n";
     s += "    double obj_lo = from_bits(0x7FF0000000000000LL);\n";
-    s += "    double ub = from_bits(0x7FF0000000000000LL);\n";
+    s += "    double fco = from_bits(0x7FF0000000000000LL);\n";
     s += "    if (s.valid) {\n";
     s += "      unsigned int kk = s.k;\n";
-    for (int i = 0; i < n; ++i) {
-        s += "      { iv X; double c; decode_dim(s.rec, " + S(n) + ", " + S(i) + ", kk, X, c);";
-        auto itX = B.vid.find("X" + S(i));
-        auto itc = B.vid.find("c" + S(i));
-        if (itX != B.vid.end() && pl.slot_pre.count(itX->second))
-            s += " st_st(st, ss, " + S(pl.slot_pre.at(itX->second)) + ", X);";
-        if (itc != B.vid.end() && pl.slot_pre.count(itc->second))
-            s += " st_sd(st, ss, " + S(pl.slot_pre.at(itc->second)) + ", c);";
-        s += " }\n";
+    for (int i = 0; i < n; ++i)
+        s += "      { iv X; double c; decode_dim(s.rec, " + S(n) + ", " + S(i) + ", kk, X, c); st_st(st, ss, " +
+             S(slot_X(n, i)) + ", X); st_sd(st, ss, " + S(slot_c(n, i)) + ", c); }\n";
+    // with `sync`, the threads of a group wait for each other after every
+    // chunk (named barrier 1 + group of blockDim / T threads), so the warps of a
+    // group run the same chunk's code together and share the instruction
+    // cache; a lane without a subdomain skips the chunk but not the barrier
+    auto calls = [&](int prog, int g, const std::string& ind) {
+        std::string r;
+        for (int c = pl.prog_first[prog]; c < pl.prog_first[prog] + pl.prog_count[prog]; ++c) {
+            if (sync)
+                r += ind + "if (s.valid) ivb_ck" + S(c) + "(st, ss);\n" + ind + "asm volatile(\"bar.sync " + S(1 + g) +
+                     ", %0;\" :: \"r\"(per) : \"memory\");\n";
+            else r += ind + "ivb_ck" + S(c) + "(st, ss);\n";
+        }
+        return r;
+    };
+    const int p0 = B.shared_point ? 1 : 0;   // program index of output 0
+    if (sync) s += "    }\n";                  // the calls run outside the valid branch
+    const std::string ind = sync ? "    " : "      ";
+    if (B.shared_point) s += calls(0, 0, ind);
+    for (int g = 0; g < T; ++g) {
+        s += ind + (g ? "else if" : "if") + " (grp == " + S(g) + ") {\n";
+        for (int o : groups[g]) {
+            s += calls(p0 + o, g, ind + "  ");
+            const std::string in2 = ind + "  " + (sync ? "if (s.valid) " : "");
+            s += in2 + "{\n";
+            s += ind + "    F" + S(o) + " = st_ld(st, ss, " + S(slot_F(n, o)) + ");\n";
+            s += ind + "    if (excludes_feasible(" + S(B.P.out_kind[o]) + "u, F" + S(o) + ")) fl |= 1u;\n";
+            if (B.P.out_kind[o] == OUT_INEQ)
+                s += ind + "    if (!le0(st_ld(st, ss, " + S(slot_fc(n, o)) + ").hi)) fl |= 2u;\n";
+            if (o == obj) {
+                s += ind + "    obj_lo = F" + S(o) + ".lo;\n";
+                s += ind + "    fco = st_ld(st, ss, " + S(slot_fc(n, o)) + ").hi;\n";
+            }
+            s += ind + "  }\n";
+        }
+        s += ind + "}\n";
     }
-    for (size_t c = 0; c < pl.chunks.size(); ++c) s += "      ivb_ck" + S(c) + "(st, ss);\n";
-    const std::map<int, int>& fin = pl.slot_after.empty() ? pl.slot_pre : pl.slot_after.back();
-    s += std::string("      bool feas = ") + (B.P.has_eq ? "false" : "true") + ";\n";
-    for (int o = 0; o < no; ++o) {
-        s += "      F" + S(o) + " = st_ld(st, ss, " + S(fin.at(B.vid.at("F" + S(o)))) + ");\n";
-        s += "      if (excludes_feasible(" + S(B.P.out_kind[o]) + "u, F" + S(o) + ")) cert = true;\n";
-        if (o == B.P.obj) s += "      obj_lo = F" + S(o) + ".lo;\n";
-        if (B.P.out_kind[o] == OUT_INEQ)
-            s += "      if (!le0(st_ld(st, ss, " + S(fin.at(B.vid.at("fc" + S(o)))) + ").hi)) feas = false;\n";
+    if (!sync) s += "    }\n";
+    if (T > 1) {
+        s += "    s_fl[threadIdx.x] = (unsigned char)fl;\n";
+        s += "    __syncthreads();\n";
+        s += "    if (grp == " + S(gobj) + ") for (int h = 0; h < " + S(T) + "; ++h) fl |= s_fl[h * per + threadIdx.x % per];\n";
+        s += "    __syncthreads();\n";
     }
-    s += "      if (feas) ub = st_ld(st, ss, " + S(fin.at(B.vid.at("fc" + S(B.P.obj)))) + ").hi;\n";
-    s += "      if (cert) obj_lo = from_bits(0x7FF0000000000000LL);\n";
+    s += "    double ub = from_bits(0x7FF0000000000000LL);\n";
+    s += "    if (s.valid && grp == " + S(gobj) + ") {\n";
+    s += std::string("      if (") + (B.P.has_eq ? "false" : "!(fl & 2u)") + ") ub = fco;\n";
+    s += "      if (fl & 1u) obj_lo = from_bits(0x7FF0000000000000LL);\n";
     s += "    }\n";
-    for (int o = 0; o < no; ++o) s += "    reduce_output(P, s, " + S(no) + ", " + S(o) + ", F" + S(o) + ");\n";
-    s += "    reduce_extras(P, s, " + S(no) + ", ub, obj_lo);\n";
+    for (int g = 0; g < T; ++g) {
+        s += std::string("    ") + (g ? "else if" : "if") + " (grp == " + S(g) + ") {\n";
+        for (int o : groups[g]) s += "      reduce_output(P, s, " + S(no) + ", " + S(o) + ", F" + S(o) + ");\n";
+        if (g == gobj) s += "      reduce_extras(P, s, " + S(no) + ", ub, obj_lo);\n";
+        s += "    }\n";
+    }
     s += "  });\n}\n";
     return s;
+}
+
+// output groups for T threads per subdomain: largest estimated work first to
+// the least loaded group, each group's outputs in index order
+std::vector<std::vector<int>> group_outputs(const Builder& B, int T) {
+    const int p0 = B.shared_point ? 1 : 0;
+    std::vector<int> order(B.no);
+    for (int o = 0; o < B.no; ++o) order[o] = o;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return B.progs[p0 + a].cost > B.progs[p0 + b].cost; });
+    std::vector<std::vector<int>> g(T);
+    std::vector<double> load(T, 0.0);
+    for (int o : order) {
+        const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        g[k].push_back(o);
+        load[k] += B.progs[p0 + o].cost;
+    }
+    for (auto& v : g) std::sort(v.begin(), v.end());
+    return g;
 }
 
 // every "Used N registers" (max) and "N bytes spill stores" (sum) in a ptxas log
@@ -671,24 +766,56 @@ SegSource jit_seg_source(const HostProgram& P, const std::vector<Ins>& ins, cons
                          const std::vector<double>& consts, int block_max, int min_blocks, int emulate, int form,
                          const SegPolicy& pol) {
     Builder B{P, ins.data(), rins.data(), consts.data(), P.n_vars, P.n_out, form, form == 1};
-    for (int i = 0; i < B.n; ++i) { B.var("X" + S(i)); B.var("c" + S(i), V_DBL); }
+    const int n = B.n, no = B.no;
+    std::map<int, int> fixed;
+    for (int i = 0; i < n; ++i) {
+        fixed[B.var("X" + S(i))] = slot_X(n, i);
+        fixed[B.var("c" + S(i), V_DBL)] = slot_c(n, i);
+    }
+    for (int o = 0; o < no; ++o) {
+        fixed[B.var("F" + S(o))] = slot_F(n, o);
+        fixed[B.var("fc" + S(o))] = slot_fc(n, o);
+    }
     B.build();
     Plan pl;
-    pl.chunks = cut(B, pol.chunk_cost, pol.chunk_stmts, B.nie_only ? 0 : pol.recompute, &pl.recomputed);
-    std::vector<int> pro, epi;
-    for (int i = 0; i < B.n; ++i) { pro.push_back(B.vid.at("X" + S(i))); pro.push_back(B.vid.at("c" + S(i))); }
-    for (int o = 0; o < B.no; ++o) {
-        epi.push_back(B.vid.at("F" + S(o)));
-        if (P.out_kind[o] == OUT_INEQ || o == P.obj) epi.push_back(B.vid.at("fc" + S(o)));
-    }
-    plan_state(B, pl, pro, epi);
+    pl.n_slots = 2 * n + 2 * no;
     SegSource out;
+    for (const Builder::Prog& pr : B.progs) {
+        long long rec = 0;
+        std::vector<Chunk> ch = cut(B, pr.st, pol.chunk_cost, pol.chunk_stmts, B.nie_only ? 0 : pol.recompute, &rec);
+        std::set<int> ends;
+        if (pr.out < 0) {
+            for (int o = 0; o < no; ++o) ends.insert(B.vid.at("fc" + S(o)));
+        } else {
+            ends.insert(B.vid.at("F" + S(pr.out)));
+            if (!B.shared_point) ends.insert(B.vid.at("fc" + S(pr.out)));
+        }
+        pl.prog_first.push_back((int)pl.chunks.size());
+        pl.prog_count.push_back((int)ch.size());
+        const std::string e = plan_prog(B, ch, fixed, ends, 2 * n + 2 * no, pl);
+        if (!e.empty()) { out.error = e; return out; }
+        pl.chunks.insert(pl.chunks.end(), ch.begin(), ch.end());
+        pl.recomputed += rec;
+    }
     out.state_units = 2 * std::max(pl.n_slots, 1);
     out.chunks = (int)pl.chunks.size();
     out.loads = pl.loads;
     out.stores = pl.stores;
     out.recomputed = pl.recomputed;
-    out.kernel = kernel_unit(B, pl, block_max, min_blocks, emulate);
+    // kernels: T = 1, and T = 2, 4 threads per subdomain when the outputs have
+    // programs of their own and there are at least T of them
+    std::string k = unit_head(emulate, true);
+    for (size_t c = 0; c < pl.chunks.size(); ++c)
+        k += "extern \"C\" __device__ void ivb_ck" + S(c) + "(double* __restrict__ st, const int ss);\n";
+    for (int T : {1, 2, 4}) {
+        if (T > 1 && (B.shared_point || no < T || block_max < 32 * T)) continue;
+        out.ts.push_back(T);
+        const std::vector<std::vector<int>> groups = group_outputs(B, T);
+        k += kernel_fn(B, pl, groups, T, false, T == 1 ? "ivb_jit_bound" : "ivb_jit_bound_t" + S(T), block_max,
+                       min_blocks);
+        k += kernel_fn(B, pl, groups, T, true, "ivb_jit_bound_t" + S(T) + "_sync", block_max, min_blocks);
+    }
+    out.kernel = k;
     // chunks spread over units of similar size, compiled in parallel
     const int C = (int)pl.chunks.size();
     const int U = std::max(1, std::min(C, pol.units));
@@ -703,6 +830,7 @@ SegSource jit_seg_source(const HostProgram& P, const std::vector<Ins>& ins, cons
 
 std::string jit_seg_compile(const SegSource& src, int max_regs, std::vector<char>& cubin, std::string& tables_name,
                             double* seconds, int* registers, int* spill_bytes) {
+    if (!src.error.empty()) return src.error;
     const auto t0 = std::chrono::steady_clock::now();
     const int U = (int)src.units.size();
     std::vector<UnitResult> res(U + 1);

@@ -27,7 +27,7 @@ struct KParams {
     const char* queue;     // device node queue (layout above)
     int32_t rec_bytes;
     unsigned long long* counter;   // work counter: first global index to hand out
-    int32_t tile;          // subdomains a block takes at a time (multiple of blockDim)
+    int32_t tile;          // subdomains a block takes at a time (multiple of its subdomains per pass)
     // per-thread frames (interpreter only)
     double* gframe;        // global frames: frame_units * blockDim per block
     int32_t frame_in_smem;

@@ -37,7 +37,14 @@ class ivb_options(ctypes.Structure):
                 ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("max_nodes", ctypes.c_int32), ("frame_in_shared", ctypes.c_int32), ("specialize", ctypes.c_int32),
                 ("emulate", ctypes.c_int32), ("recompute", ctypes.c_int32), ("seg_chunk", ctypes.c_int32),
-                ("seg_regs", ctypes.c_int32)]
+                ("seg_regs", ctypes.c_int32), ("threads_per_subdomain", ctypes.c_int32), ("seg_sync", ctypes.c_int32)]
+
+
+class ivb_tuning(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("frame_in_shared", ctypes.c_int32), ("threads_per_subdomain", ctypes.c_int32),
+                ("subdomains_per_pass", ctypes.c_int32), ("chunk_sync", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("best_ms", ctypes.c_float), ("worst_ms", ctypes.c_float)]
 
 
 class ivb_tape(ctypes.Structure):
@@ -55,7 +62,7 @@ class ivb_bnb_options(ctypes.Structure):
 class ivb_bnb_result(ctypes.Structure):
     _fields_ = [("lb", ctypes.c_double), ("ub", ctypes.c_double), ("iterations", ctypes.c_int64),
                 ("nodes_bounded", ctypes.c_int64), ("subdomains", ctypes.c_int64), ("seconds", ctypes.c_double),
-                ("converged", ctypes.c_int32), ("open_nodes", ctypes.c_int64)]
+                ("converged", ctypes.c_int32), ("open_nodes", ctypes.c_int64), ("split_target", ctypes.c_int64)]
 
 
 _lib = None
@@ -99,10 +106,11 @@ def lib() -> ctypes.CDLL:
         L.ivb_host_gradient.argtypes = [P, P, I32, I32, P]
         L.ivb_specialize_compile.argtypes = [P, I32, I32, P, P, P]
         L.ivb_get_segmentation.argtypes = [P, P, P, P, P, P, P]
+        L.ivb_get_tuning_ex.argtypes = [P, P]
         for f in ("ivb_create_problem", "ivb_bound_nodes", "ivb_bound_nodes_ex", "ivb_enclose", "ivb_point_grad",
                   "ivb_pick_splits", "ivb_get_tuning", "ivb_bnb_solve", "ivb_op_counts", "ivb_fp64_probe",
                   "ivb_bound_nodes_noalloc", "ivb_eval_op", "ivb_get_specialization", "ivb_specialize_compile",
-                  "ivb_get_segmentation",
+                  "ivb_get_segmentation", "ivb_get_tuning_ex",
                   "ivb_propagate", "ivb_host_gradient"):
             getattr(L, f).restype = I32
         _lib = L
@@ -417,13 +425,12 @@ class Problem:
                self._h)
         return {"lb": r.lb, "ub": r.ub, "iterations": r.iterations, "nodes": r.nodes_bounded,
                 "subdomains": r.subdomains, "seconds": r.seconds, "converged": bool(r.converged),
-                "open": r.open_nodes}
+                "open": r.open_nodes, "split_target": r.split_target}
 
     def ivb_get_tuning(self):
-        v = [ctypes.c_int32() for _ in range(4)]
-        _check(lib().ivb_get_tuning(self._h, *[ctypes.byref(x) for x in v]), self._h)
-        return {"block_threads": v[0].value, "blocks_per_sm": v[1].value, "tile": v[2].value,
-                "frame_in_shared": v[3].value}
+        t = ivb_tuning()
+        _check(lib().ivb_get_tuning_ex(self._h, ctypes.byref(t)), self._h)
+        return {k: getattr(t, k) for k, _ in ivb_tuning._fields_}
 
     def ivb_get_specialization(self) -> dict:
         a, r, lb, sec, em = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double(), ctypes.c_int32()

@@ -159,3 +159,107 @@ def test_segmented_full_scale_config5_identical_to_interpreter():
             res.append(p.bound_nodes_ex(boxes, splits, want_hull=True))
     for k in KEYS:
         assert same_bits(res[0][k], res[1][k]), k
+
+
+# ------------------------------------------- the autotuner's launch knobs
+
+@pytest.mark.parametrize("tpsub", [1, 2, 4])
+@pytest.mark.parametrize("path", ["graph", "plain"])
+def test_threads_per_subdomain_bit_exact_rational(tpsub, path):
+    """1, 2 or 4 threads share each subdomain (output groups in different
+    warps, flags combined in shared memory): the ragged batch's lb, ub,
+    flags and hulls equal the oracle's bit for bit"""
+    t = rational_problem(n=3, K=50, n_ineq=3)
+    boxes, splits = ragged_batch(t, 37, seed=13)
+    opts = dict(grad_mode="adjoint", specialize=3, seg_chunk=24, threads_per_subdomain=tpsub,
+                use_graph=int(path == "graph"), batched=int(path != "plain"))
+    with ivb.Problem(t, **opts) as p:
+        r = p.bound_nodes_ex(boxes, splits, want_hull=True)
+        assert p.get_tuning()["threads_per_subdomain"] == tpsub
+    ref = oracle.bound_nodes(t, boxes, splits, grad_mode="adjoint", tight=True)
+    for k in ("lb", "ub", "minlo", "maxhi"):
+        assert np.array_equal(r[k], ref[k]), k
+    assert np.array_equal(r["infeasible"].astype(bool), ref["infeasible"])
+
+
+@pytest.mark.parametrize("kind", ["feasible", "infeasible", "eq_in"])
+def test_threads_per_subdomain_filter_and_ub(kind):
+    """the tests that need every output of a subdomain (filtered objective,
+    certified-feasible centre) across two output groups"""
+    t = P.constrained_toy(kind)
+    boxes = W.bisection_frontier(t.root_box, 9, seed=2)
+    splits = np.array([[6, 5]] * 9, np.int32)
+    with ivb.Problem(t, filter=1, specialize=3, threads_per_subdomain=2) as p:
+        r = p.bound_nodes_ex(boxes, splits, want_hull=True)
+        assert p.get_tuning()["threads_per_subdomain"] == 2
+    ref = oracle.bound_nodes(t, boxes, splits, filter=True)
+    for k in ("lb", "ub", "minlo", "maxhi"):
+        assert np.array_equal(r[k], ref[k]), k
+    assert np.array_equal(r["infeasible"].astype(bool), ref["infeasible"])
+
+
+def test_every_launch_candidate_gives_identical_bounds():
+    """threads per subdomain x block size x subdomains per grab x chunk
+    synchronisation, fixed by options (no timing): every combination the
+    autotuner can pick gives the interpreter's bits on configuration 2
+    (exp/log tape)"""
+    t = W.config_tape(2)
+    boxes, splits = ragged_batch(t, 23, seed=5)
+    with ivb.Problem(t, grad_mode="adjoint", specialize=0) as p:
+        ref = p.bound_nodes_ex(boxes, splits, want_hull=True)
+    seen = set()
+    for sync in (0, 1):
+        for tpsub in (1, 2, 4):
+            for block, mult in ((64, 1), (128, 4), (256, 16)):
+                if block < 32 * tpsub:
+                    continue
+                per = block // tpsub
+                with ivb.Problem(t, grad_mode="adjoint", specialize=3, threads_per_subdomain=tpsub,
+                                 block_threads=block, blocks_per_sm=2, tile=mult * per, seg_sync=sync) as p:
+                    r = p.bound_nodes_ex(boxes, splits, want_hull=True)
+                    tun = p.get_tuning()
+                assert (tun["threads_per_subdomain"], tun["block_threads"], tun["tile"], tun["chunk_sync"]) == \
+                    (tpsub, block, mult * per, sync)
+                seen.add((sync, tpsub, block, mult))
+                for k in KEYS:
+                    assert same_bits(ref[k], r[k]), (sync, tpsub, block, mult, k)
+    assert len(seen) == 16
+
+
+def test_autotuner_full_size_choice_reported_and_identical():
+    """configuration 2 at full size (16 nodes x 16^4): the autotuner times
+    threads per subdomain, block size, blocks per SM and grab size, reports
+    its choice, and the bounds equal the interpreter's"""
+    wl = W.config_workload(2)
+    t = wl.tape
+    boxes = W.bisection_frontier(t.root_box, 16, seed=20)
+    splits = np.tile(wl.splits, (16, 1)).astype(np.int32)
+    out = []
+    for spec in (0, 3):
+        with ivb.Problem(t, grad_mode="adjoint", specialize=spec) as p:
+            out.append(p.bound_nodes_ex(boxes, splits, want_hull=True))
+            tun = p.get_tuning()
+        if spec == 3:
+            assert tun["candidates"] > 10 and tun["threads_per_subdomain"] in (1, 2, 4)
+            assert tun["tile"] % tun["subdomains_per_pass"] == 0
+            assert tun["subdomains_per_pass"] * tun["threads_per_subdomain"] == tun["block_threads"]
+            assert 0 < tun["best_ms"] <= tun["worst_ms"]
+    for k in KEYS:
+        assert same_bits(out[0][k], out[1][k]), k
+
+
+def test_bnb_split_target_picked_from_the_launch():
+    """B&B with the split picker and target 0: each iteration's target is
+    the smallest power of two >= 2^8 (at most 2^20) that makes its children
+    cover four waves of the launch; an explicit target is used as given"""
+    t = rational_problem(n=2, K=40, n_ineq=1, seed=99)
+    with ivb.Problem(t, grad_mode="adjoint", specialize=3) as p:
+        r = p.bnb_solve(t.root_box, target=0, strategy="adaptive", batch=4, eps_rel=1e-4, max_nodes=64)
+        tun = p.get_tuning()
+        r2 = p.bnb_solve(t.root_box, target=1000, strategy="adaptive", batch=4, eps_rel=1e-4, max_nodes=64)
+    tgt = r["split_target"]
+    assert 256 <= tgt <= 1 << 20 and tgt & (tgt - 1) == 0
+    wave = torch.cuda.get_device_properties(0).multi_processor_count * tun["blocks_per_sm"] * tun["subdomains_per_pass"]
+    assert tgt == 1 << 20 or tgt * 8 >= 4 * wave
+    assert r2["split_target"] == 1000
+    assert r["lb"] <= r["ub"] and r2["lb"] <= r2["ub"]
