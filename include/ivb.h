@@ -162,6 +162,10 @@ typedef struct {
                                   share the instruction cache), 0 they run
                                   freely; -1 (default): chosen by the
                                   autotuner                                  */
+    int32_t seg_ilp;           /* segmented kernel: subdomains per thread,
+                                  1 or 2 (two independent dependency chains
+                                  per thread, every statement run on both
+                                  interleaved); 0 (default): 1              */
 } ivb_options;
 
 typedef struct ivb_problem ivb_problem;
@@ -357,7 +361,8 @@ typedef struct {
                                       subdomains per pass)                      */
     int32_t frame_in_shared;       /* interpreter frames in shared memory (0/1)  */
     int32_t threads_per_subdomain; /* threads sharing one subdomain's outputs    */
-    int32_t subdomains_per_pass;   /* block_threads / threads_per_subdomain      */
+    int32_t subdomains_per_pass;   /* block_threads / threads_per_subdomain x
+                                      subdomains per thread                     */
     int32_t chunk_sync;            /* segmented kernel: groups kept on one chunk */
     int32_t candidates;            /* launch configurations timed (0: none)      */
     float best_ms, worst_ms;       /* their times on the tuning sample           */
@@ -374,11 +379,11 @@ ivb_status ivb_get_specialization(ivb_problem* p, int32_t* active, int32_t* regi
 /* The segmented kernel of a problem (specialize = 3; each may be NULL):
  * doubles of per-thread state, chunk functions, state loads and stores per
  * subdomain (intervals and centre coordinates), forward operations recomputed
- * per subdomain by the reverse chunks, and the recomputation policy compiled
- * in. Zeros when the problem has no segmented kernel. Not part of the
+ * per subdomain by the reverse chunks, the recomputation policy compiled in,
+ * and the subdomains each thread runs at once (seg_ilp). Zeros when the problem has no segmented kernel. Not part of the
  * paper's method: reports how the bounds are computed. */
 ivb_status ivb_get_segmentation(ivb_problem* p, int32_t* state_units, int32_t* chunks, int64_t* state_loads,
-                                int64_t* state_stores, int64_t* recomputed, int32_t* recompute);
+                                int64_t* state_stores, int64_t* recomputed, int32_t* recompute, int32_t* ilp);
 
 /* Generate and compile (NVRTC, sm_103a) the tape-specialised kernel of a
  * tape without loading it -- needs no GPU; compact = 1 as for specialize = 1,

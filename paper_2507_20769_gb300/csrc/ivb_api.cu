@@ -218,6 +218,12 @@ struct TuneCand {
     bool sync;
 };
 
+// subdomains a block covers per pass of its tile loop
+int pass_size(const ivb_problem* p, int block, int tpsub) {
+    const int ilp = use_jit(p) && p->jit.state_units > 0 ? p->jit.ilp : 1;
+    return block / std::max(1, tpsub) * ilp;
+}
+
 // threads-per-subdomain values the loaded kernel offers (1 unless segmented)
 std::vector<int> tpsub_choices(const ivb_problem* p) {
     std::vector<int> v{1};
@@ -285,7 +291,7 @@ ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
         ivb_status r = IVB_OK;
         if (reduce_units(p) > 0) r = ensure_frame(p, grid, c.block, reduce_units(p));
         if (r) return r;
-        const int tile = c.tile_mult * (c.block / c.tpsub);
+        const int tile = c.tile_mult * pass_size(p, c.block, c.tpsub);
         for (int rep = 0; rep < 2; ++rep) {      // warm-up, then timed
             if (rep == 1) { cudaError_t ce = cudaEventRecord(e0, s); if (ce) return cuda_fail(p, ce, "event"); }
             r = enqueue_bound(p, grid, c.block, tile, c.smem, p->max_nodes, s, c.tpsub, c.sync);
@@ -325,7 +331,7 @@ ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
     p->frame_smem = bc.smem;
     p->tpsub = bc.tpsub;
     p->chunk_sync = bc.sync;
-    p->tile = bc.tile_mult * (bc.block / bc.tpsub);
+    p->tile = bc.tile_mult * pass_size(p, bc.block, bc.tpsub);
     p->tune_candidates = timed;
     p->tune_best_ms = best;
     p->tune_worst_ms = worst;
@@ -349,7 +355,7 @@ ivb_status default_tuning(ivb_problem* p) {
     const int occ = reduce_occupancy(p, p->block, p->frame_smem, p->tpsub, p->chunk_sync);
     if (occ < 1) return fail(p, IVB_ENOTSUP, "launch configuration does not fit on an SM");
     if (p->bps > occ) p->bps = occ;
-    const int per = p->block / p->tpsub;
+    const int per = pass_size(p, p->block, p->tpsub);
     p->tile = p->opt.tile > 0 ? ((p->opt.tile + per - 1) / per) * per : per;
     p->cfg_ready = true;
     const bool explicit_cfg = p->opt.block_threads > 0 || p->opt.blocks_per_sm > 0;
@@ -387,6 +393,7 @@ SegPolicy seg_policy(const ivb_options& o) {
     SegPolicy pol;
     if (o.recompute >= 0) pol.recompute = o.recompute;
     if (o.seg_chunk > 0) pol.chunk_cost = o.seg_chunk;
+    if (o.seg_ilp > 0) pol.ilp = o.seg_ilp;
     if (o.seg_regs > 0) pol.max_regs = o.seg_regs;
     const unsigned hc = std::thread::hardware_concurrency();
     pol.units = std::max(1, std::min(64, hc ? (int)hc : 8));
@@ -430,6 +437,7 @@ cudaError_t specialize_seg(ivb_problem* p, const std::vector<Ins>& ins, const st
     p->jit.state_stores = src.stores;
     p->jit.recomputed = src.recomputed;
     p->jit.recompute = pol.recompute;
+    p->jit.ilp = src.ilp;
     return cudaSuccess;
 }
 
@@ -474,6 +482,7 @@ extern "C" void ivb_options_default(ivb_options* o) {
     o->seg_regs = 0;
     o->threads_per_subdomain = 0;
     o->seg_sync = -1;
+    o->seg_ilp = 0;
 }
 
 extern "C" ivb_status ivb_create_problem(const ivb_tape* tape, const ivb_options* opt, ivb_problem** out) {
@@ -499,6 +508,7 @@ extern "C" ivb_status ivb_create_problem(const ivb_tape* tape, const ivb_options
         o.threads_per_subdomain != 4)
         return fail(nullptr, IVB_EINVAL, "threads_per_subdomain must be 0 (tuned), 1, 2 or 4");
     if (o.seg_sync < -1 || o.seg_sync > 1) return fail(nullptr, IVB_EINVAL, "seg_sync must be -1, 0 or 1");
+    if (o.seg_ilp < 0 || o.seg_ilp > 2) return fail(nullptr, IVB_EINVAL, "seg_ilp must be 0, 1 or 2");
     if (o.seg_regs != 0 && (o.seg_regs < 64 || o.seg_regs > 255))
         return fail(nullptr, IVB_EINVAL, "seg_regs must be 0 or in [64, 255]");
     if (o.emulate < -1 || o.emulate > 15) return fail(nullptr, IVB_EINVAL, "emulate must be -1 or a bitmask in [0, 15]");
@@ -672,7 +682,7 @@ ivb_status bound_nodes_impl(ivb_problem* p, int32_t n_nodes, const double* boxes
             CK(launch_init_keys(p->d_keys, p->d_queue, 1, p->n_out, s));
             CK(cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned long long), s));
             KParams K = make_params(p, p->frame_smem);
-            K.tile = p->block / p->tpsub;
+            K.tile = pass_size(p, p->block, p->tpsub);
             CK(launch_reduce(p, K, grid, p->block, p->frame_smem, s, p->tpsub, p->chunk_sync));
             FinalizeParams F{};
             F.keys = p->d_keys; F.queue = p->d_queue; F.max_nodes = 1; F.n_out = p->n_out; F.obj = p->obj;
@@ -892,7 +902,7 @@ extern "C" ivb_status ivb_get_tuning_ex(ivb_problem* p, ivb_tuning* t) {
     t->frame_in_shared = p->frame_smem;
     t->threads_per_subdomain = p->tpsub;
     t->chunk_sync = p->chunk_sync ? 1 : 0;
-    t->subdomains_per_pass = p->block / std::max(1, p->tpsub);
+    t->subdomains_per_pass = pass_size(p, p->block, p->tpsub);
     t->candidates = p->tune_candidates;
     t->best_ms = p->tune_best_ms;
     t->worst_ms = p->tune_worst_ms;
@@ -912,7 +922,7 @@ extern "C" ivb_status ivb_get_specialization(ivb_problem* p, int32_t* active, in
 
 extern "C" ivb_status ivb_get_segmentation(ivb_problem* p, int32_t* state_units, int32_t* chunks,
                                            int64_t* state_loads, int64_t* state_stores, int64_t* recomputed,
-                                           int32_t* recompute) {
+                                           int32_t* recompute, int32_t* ilp) {
     if (!p) return fail(nullptr, IVB_EINVAL, "problem handle is NULL");
     const bool seg = use_jit(p) && p->jit.state_units > 0;
     if (state_units) *state_units = seg ? p->jit.state_units : 0;
@@ -921,6 +931,7 @@ extern "C" ivb_status ivb_get_segmentation(ivb_problem* p, int32_t* state_units,
     if (state_stores) *state_stores = seg ? p->jit.state_stores : 0;
     if (recomputed) *recomputed = seg ? p->jit.recomputed : 0;
     if (recompute) *recompute = seg ? p->jit.recompute : 0;
+    if (ilp) *ilp = seg ? p->jit.ilp : 0;
     return IVB_OK;
 }
 

@@ -172,7 +172,9 @@ extern "C" ivb_status ivb_bnb_solve(ivb_problem* p, int32_t n, const double* roo
         // this iteration's children cover four waves of the bounding launch
         int64_t target = o->target;
         if (o->split_mode > 0 && target == 0) {
-            const int64_t wave = (int64_t)p->sm_count * std::max(1, p->bps) * (std::max(1, p->block) / std::max(1, p->tpsub));
+            const int ilp = p->jit.kern && p->jit.state_units > 0 ? p->jit.ilp : 1;
+            const int64_t wave =
+                (int64_t)p->sm_count * std::max(1, p->bps) * (std::max(1, p->block) / std::max(1, p->tpsub)) * ilp;
             const int64_t want = (4 * wave + cnt - 1) / std::max(1, cnt);
             target = 1 << 8;
             while (target < want && target < (1 << 20)) target <<= 1;

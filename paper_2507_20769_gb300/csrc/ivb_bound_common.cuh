@@ -125,6 +125,58 @@ __device__ __forceinline__ void tile_loop(const KParams& P, Body&& body) {
     tile_loop_per(P, (int)blockDim.x, body);
 }
 
+// the lane's subdomain g of [.., end): node by binary search over the prefix
+// offsets, index inside the node, record, warp uniformity
+__device__ __forceinline__ Sub make_sub(long long g, long long end, int n_nodes, const long long* off,
+                                        const char* recs, int rec_bytes) {
+    Sub s;
+    s.g = g;
+    s.valid = g < end;
+    s.node = -1;
+    s.k = 0;
+    s.rec = recs;
+    if (s.valid) {
+        int lo = 0, hi = n_nodes - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(off + mid) <= g) lo = mid; else hi = mid - 1;
+        }
+        s.node = lo;
+        s.k = (unsigned int)(g - __ldg(off + lo));
+        s.rec = recs + (long long)lo * rec_bytes;
+    }
+    const int node0 = __shfl_sync(0xFFFFFFFFu, s.node, 0);
+    s.uniform = __all_sync(0xFFFFFFFFu, !s.valid || s.node == node0);
+    return s;
+}
+
+// As tile_loop_per with two subdomains per thread per pass: g0 + t % per and
+// g0 + per + t % per, so a pass covers 2 per subdomains (the tile is a
+// multiple of 2 per); body(s0, s1) with s1 invalid where the range ends.
+template <class Body>
+__device__ __forceinline__ void tile_loop_per2(const KParams& P, const int per, Body&& body) {
+    const long long* qh = reinterpret_cast<const long long*>(P.queue);
+    const int n_nodes = (int)qh[0];
+    const long long total = qh[1];
+    const long long* off = reinterpret_cast<const long long*>(P.queue + kQueueHeader);
+    const char* recs = P.queue + kQueueHeader + 8 * (long long)(n_nodes + 1);
+    __shared__ long long s_base2;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_base2 = (long long)atomicAdd(P.counter, (unsigned long long)P.tile);
+        __syncthreads();
+        const long long base = s_base2;
+        if (base >= total) break;
+        const long long end = base + P.tile < total ? base + P.tile : total;
+        const long long lane = (long long)(threadIdx.x % (unsigned)per);
+        for (long long g0 = base; g0 < end; g0 += 2 * (long long)per) {
+            const Sub s0 = make_sub(g0 + lane, end, n_nodes, off, recs, P.rec_bytes);
+            const Sub s1 = make_sub(g0 + per + lane, end, n_nodes, off, recs, P.rec_bytes);
+            body(s0, s1);
+        }
+    }
+}
+
 // Step 1 for dimension i (Section 2.2 splitting item i): j = kk mod N_i, then
 // kk /= N_i; endpoints lo + j h and lo + (j + 1) h (round to nearest, clamped
 // to the node, the node's own ends at j = 0 and j = N_i - 1) and the centre

@@ -43,7 +43,7 @@ struct JitKernel {
     // segmented kernels (ivb_jit_seg.cpp): per-thread state area in doubles
     // (0 for the other variants), chunks, state loads and stores and
     // recomputed forward operations per subdomain, recomputation policy
-    int state_units = 0, chunks = 0, recompute = -1;
+    int state_units = 0, chunks = 0, recompute = -1, ilp = 1;
     long long state_loads = 0, state_stores = 0, recomputed = 0;
     // kernels of the segmented variant for 1, 2 and 4 threads per subdomain
     // (index 0, 1, 2; nullptr where not compiled), without and with the
@@ -64,12 +64,13 @@ struct SegPolicy {
     int recompute = 1;
     int units = 16;
     int max_regs = 128;          // register budget of every chunk function
+    int ilp = 1;                 // subdomains per thread (1, or 2 interleaved)
 };
 struct SegSource {
     std::string kernel;               // tile loop, Step 1, chunk calls, Step 3 (one kernel per T)
     std::vector<std::string> units;   // the chunk functions
     std::vector<int> ts;              // threads per subdomain with a kernel: ivb_jit_bound (1), _t2, _t4
-    int state_units = 0, chunks = 0;
+    int state_units = 0, chunks = 0, ilp = 1;
     long long loads = 0, stores = 0, recomputed = 0;
     std::string error;                // "" unless the program could not be planned
 };

@@ -125,15 +125,15 @@ struct Builder {
         if (kind == K_SLOT) {
             const std::string nm = std::string(1, role) + S(idx);
             reads.push_back(var(nm));
-            return nm;
+            return nm + "$";
         }
         if (kind == K_VAR) {
             if (role == 'p' || role == 'q') {
                 reads.push_back(var("c" + S(idx), V_DBL));
-                return "mk(c" + S(idx) + ", c" + S(idx) + ")";
+                return "mk(c" + S(idx) + "$, c" + S(idx) + "$)";
             }
             reads.push_back(var("X" + S(idx)));
-            return "X" + S(idx);
+            return "X" + S(idx) + "$";
         }
         return konst(idx);
     }
@@ -160,7 +160,7 @@ struct Builder {
         const std::string B = bk != K_NONE ? val(role, bk, I.w1 >> 16, s.reads) : A;
         const std::string D = std::string(1, role) + S(dst);
         s.writes.push_back(var(D));
-        s.code = D + " = " + eval(op, A, B) + ";";
+        s.code = D + "$ = " + eval(op, A, B) + ";";
         s.cost = op_cost(op);
         s.op = op;
         s.phase = role == 'r' ? 1 : 0;
@@ -173,13 +173,13 @@ struct Builder {
         Stmt s;
         s.phase = 2;
         const uint32_t op = R.w0 & 31u, wslot = R.w0 >> 16;
-        const std::string W = "w" + S(wslot);
-        s.reads.push_back(var(W));
+        const std::string W = "w" + S(wslot) + "$";
+        s.reads.push_back(var("w" + S(wslot)));
         if (op == OP_VAR) {
             const std::string g = "g" + S(R.w1);
             s.reads.push_back(var(g));
             s.writes.push_back(var(g));
-            s.code = g + " = iv_add(" + g + ", " + W + ");";
+            s.code = g + "$ = iv_add(" + g + "$, " + W + ");";
             s.cost = 2.0;
             return s;
         }
@@ -222,22 +222,22 @@ struct Builder {
         if (!b_none && b_prod) body += "const iv yb = " + by + "; ";
         std::string upd;
         if (!a_none) {
-            const std::string u = "w" + S(R.w1 & 0xFFFFu);
+            const std::string un = "w" + S(R.w1 & 0xFFFFu), u = un + "$";
             std::string v;
             if (a_prod) v = a_init ? "iv_mul(" + ax + ", ya)" : "iv_fma(" + ax + ", ya, " + u + ")";
             else if (a_init) v = sub_a ? "iv_neg(" + ax + ")" : ax;
             else v = sub_a ? "iv_sub(" + u + ", " + ax + ")" : "iv_add(" + u + ", " + ax + ")";
-            if (!a_init) s.reads.push_back(var(u));
+            if (!a_init) s.reads.push_back(var(un));
             upd += u + " = " + v + "; ";
             cost += (a_prod || !a_init) ? 2.0 : 0.0;
         }
         if (!b_none) {
-            const std::string u = "w" + S(R.w1 >> 16);
+            const std::string un = "w" + S(R.w1 >> 16), u = un + "$";
             std::string v;
             if (b_prod) v = b_init ? "iv_mul(" + bx + ", yb)" : "iv_fma(" + bx + ", yb, " + u + ")";
             else if (b_init) v = sub_b ? "iv_neg(" + bx + ")" : bx;
             else v = sub_b ? "iv_sub(" + u + ", " + bx + ")" : "iv_add(" + u + ", " + bx + ")";
-            if (!b_init) s.reads.push_back(var(u));
+            if (!b_init) s.reads.push_back(var(un));
             upd += u + " = " + v + "; ";
             cost += (b_prod || !b_init) ? 2.0 : 0.0;
         }
@@ -269,7 +269,7 @@ struct Builder {
         s.phase = phase;
         const std::string v = val(role, kind, ref, s.reads);
         s.writes.push_back(var(dst));
-        s.code = dst + " = " + v + ";";
+        s.code = dst + "$ = " + v + ";";
         return s;
     }
 
@@ -312,11 +312,11 @@ struct Builder {
                 t.phase = 2;
                 for (int i = 0; i < n; ++i) {
                     t.writes.push_back(var("g" + S(i)));
-                    t.code += "g" + S(i) + " = zero(); ";
+                    t.code += "g" + S(i) + "$ = zero(); ";
                 }
                 if (A.out_wslot >= 0) {
                     t.writes.push_back(var("w" + S(A.out_wslot)));
-                    t.code += "w" + S(A.out_wslot) + " = one();";
+                    t.code += "w" + S(A.out_wslot) + "$ = one();";
                 }
                 q.push_back(t);
                 for (int i = A.rv_begin; i < A.rv_begin + A.rv_count; ++i) {
@@ -332,18 +332,18 @@ struct Builder {
             const std::string F = "F" + S(o);
             if (nie_only) {
                 m.reads.push_back(var("nie" + S(o)));
-                m.code = F + " = final_form(1, nie" + S(o) + ", nie" + S(o) + ");";
+                m.code = F + "$ = final_form(1, nie" + S(o) + "$, nie" + S(o) + "$);";
             } else {
                 m.reads.push_back(var("fc" + S(o)));
-                m.code = "{ iv mvf = fc" + S(o) + "; ";
+                m.code = "{ iv mvf = fc" + S(o) + "$; ";
                 for (int i = 0; i < n; ++i) {
                     m.reads.push_back(var("g" + S(i)));
                     m.reads.push_back(var("X" + S(i)));
                     m.reads.push_back(var("c" + S(i), V_DBL));
-                    m.code += "mvf = mvf_term(mvf, g" + S(i) + ", X" + S(i) + ", c" + S(i) + "); ";
+                    m.code += "mvf = mvf_term(mvf, g" + S(i) + "$, X" + S(i) + "$, c" + S(i) + "$); ";
                 }
                 m.reads.push_back(var("nie" + S(o)));
-                m.code += F + " = final_form(" + S(form) + ", mvf, nie" + S(o) + "); }";
+                m.code += F + "$ = final_form(" + S(form) + ", mvf, nie" + S(o) + "$); }";
                 m.cost = 2.0 * n + 2.0;
             }
             m.writes.push_back(var(F));
@@ -513,8 +513,22 @@ std::string plan_prog(const Builder& B, const std::vector<Chunk>& ch, const std:
     return "";
 }
 
-// C++ of one chunk function
-std::string chunk_fn(const Builder& B, const Plan& pl, int c) {
+// a statement's code for copy k of K (variable names end in '$')
+std::string copy_code(const std::string& code, int K, int k) {
+    const std::string sfx = K > 1 ? "_" + S(k) : "";
+    std::string r;
+    r.reserve(code.size() + 16);
+    for (char ch : code) {
+        if (ch == '$') r += sfx;
+        else r += ch;
+    }
+    return r;
+}
+
+// C++ of one chunk function. With K = 2 every statement runs twice, on two
+// subdomains, interleaved: two independent dependency chains per thread.
+// Copy k keeps its values in state slots offset by k * ns.
+std::string chunk_fn(const Builder& B, const Plan& pl, int c, int K, int ns) {
     const Chunk& ch = pl.chunks[c];
     const std::map<int, int>& ld = pl.load_slot[c];
     const std::map<int, int>& stv = pl.store_slot[c];
@@ -525,12 +539,14 @@ std::string chunk_fn(const Builder& B, const Plan& pl, int c) {
         for (int v : t.reads) touched.insert(v);
         for (int v : t.writes) touched.insert(v);
     }
+    auto nm = [&](int v, int k) { return B.vname[v] + (K > 1 ? "_" + S(k) : ""); };
     {
         std::string dv, dd;
-        for (int v : touched) {
-            if (B.vtype[v] == V_DBL) dd += (dd.empty() ? "  double " : ", ") + B.vname[v];
-            else dv += (dv.empty() ? "  iv " : ", ") + B.vname[v];
-        }
+        for (int v : touched)
+            for (int k = 0; k < K; ++k) {
+                if (B.vtype[v] == V_DBL) dd += (dd.empty() ? "  double " : ", ") + nm(v, k);
+                else dv += (dv.empty() ? "  iv " : ", ") + nm(v, k);
+            }
         if (!dv.empty()) s += dv + ";\n";
         if (!dd.empty()) s += dd + ";\n";
     }
@@ -543,17 +559,21 @@ std::string chunk_fn(const Builder& B, const Plan& pl, int c) {
         // live-ins are loaded before their first read (the scheduler hoists them)
         for (int v : t.reads)
             if (!written.count(v) && !loaded.count(v)) {
-                const int slot = ld.at(v);
-                s += "  " + B.vname[v] + (B.vtype[v] == V_DBL ? " = st_d(st, ss, " : " = st_ld(st, ss, ") + S(slot) + ");\n";
+                for (int k = 0; k < K; ++k) {
+                    const int slot = ld.at(v) + k * ns;
+                    s += "  " + nm(v, k) + (B.vtype[v] == V_DBL ? " = st_d(st, ss, " : " = st_ld(st, ss, ") + S(slot) +
+                         ");\n";
+                }
                 loaded.insert(v);
             }
-        s += "  " + t.code + "\n";
+        for (int k = 0; k < K; ++k) s += "  " + copy_code(t.code, K, k) + "\n";
         for (int v : t.writes) written.insert(v);
         for (int v : t.writes) {
             auto it = stv.find(v);
             if (last_write[v] == i && it != stv.end())
-                s += std::string(B.vtype[v] == V_DBL ? "  st_sd(st, ss, " : "  st_st(st, ss, ") + S(it->second) + ", " +
-                     B.vname[v] + ");\n";
+                for (int k = 0; k < K; ++k)
+                    s += std::string(B.vtype[v] == V_DBL ? "  st_sd(st, ss, " : "  st_st(st, ss, ") +
+                         S(it->second + k * ns) + ", " + nm(v, k) + ");\n";
         }
     }
     s += "}\n";
@@ -599,11 +619,12 @@ int slot_fc(int n, int o) { return 2 * n + 2 * o + 1; }
 // bound) are combined through shared memory by the objective's group; each
 // group reduces its own outputs' hulls. T = 1 is the plain kernel.
 std::string kernel_fn(const Builder& B, const Plan& pl, const std::vector<std::vector<int>>& groups, int T,
-                      bool sync, const std::string& name, int block_max, int min_blocks) {
+                      bool sync, int K, int ns, const std::string& name, int block_max, int min_blocks) {
     const int n = B.n, no = B.no, obj = B.P.obj;
     int gobj = 0;
     for (int g = 0; g < T; ++g)
         for (int o : groups[g]) if (o == obj) gobj = g;
+    auto sub = [&](int k) { return "s" + S(k); };
     std::string s = "extern \"C\" __global__ void __launch_bounds__(" + S(block_max) + ", " + S(min_blocks) + ") " +
                     name + "(const ivb::KParams P) {\n";
     s += "  using namespace ivb;\n";
@@ -611,21 +632,28 @@ std::string kernel_fn(const Builder& B, const Plan& pl, const std::vector<std::v
     s += "  const int ss = blockDim.x;\n";
     s += "  const int per = blockDim.x / " + S(T) + ";\n";
     s += "  const int grp = threadIdx.x / per;\n";
-    if (T > 1) s += "  __shared__ unsigned char s_fl[" + S(block_max) + "];\n";
-    s += "  tile_loop_per(P, per, [&](const Sub& s) {\n";
-    {
+    if (T > 1) s += "  __shared__ unsigned char s_fl[" + S(K) + "][" + S(block_max) + "];\n";
+    if (K == 1) s += "  tile_loop_per(P, per, [&](const Sub& s0) {\n";
+    else s += "  tile_loop_per2(P, per, [&](const Sub& s0, const Sub& s1) {\n";
+    for (int k = 0; k < K; ++k) {
         std::string f = "    iv ";
-        for (int o = 0; o < no; ++o) f += (o ? ", F" : "F") + S(o) + " = zero()";
+        for (int o = 0; o < no; ++o) f += (o ? ", F" : "F") + S(o) + "_" + S(k) + " = zero()";
         s += f + ";\n";
+        s += "    unsigned int fl_" + S(k) + " = 0u;\n";
+        s += "    double obj_lo_" + S(k) + " = from_bits(0x7FF0000000000000LL), fco_" + S(k) +
+             " = from_bits(0x7FF0000000000000LL);\n";
     }
-    s += "    unsigned int fl = 0u;   // 1: an output proves the subdomain infeasible; 2: the centre is not certified feasible\n";
-    s += "    double obj_lo = from_bits(0x7FF0000000000000LL);\n";
-    s += "    double fco = from_bits(0x7FF0000000000000LL);\n";
-    s += "    if (s.valid) {\n";
-    s += "      unsigned int kk = s.k;\n";
-    for (int i = 0; i < n; ++i)
-        s += "      { iv X; double c; decode_dim(s.rec, " + S(n) + ", " + S(i) + ", kk, X, c); st_st(st, ss, " +
-             S(slot_X(n, i)) + ", X); st_sd(st, ss, " + S(slot_c(n, i)) + ", c); }\n";
+    s += "    // fl bit 1: an output proves the subdomain infeasible; bit 2: its centre is not certified feasible\n";
+    s += "    if (s0.valid) {\n";
+    for (int k = 0; k < K; ++k) {
+        // a second copy without a subdomain of its own repeats the first (its results are not reduced)
+        const std::string sk = k == 0 ? "s0" : "(s1.valid ? s1 : s0)";
+        s += "      { const Sub& d = " + sk + "; unsigned int kk = d.k;\n";
+        for (int i = 0; i < n; ++i)
+            s += "        { iv X; double c; decode_dim(d.rec, " + S(n) + ", " + S(i) + ", kk, X, c); st_st(st, ss, " +
+                 S(slot_X(n, i) + k * ns) + ", X); st_sd(st, ss, " + S(slot_c(n, i) + k * ns) + ", c); }\n";
+        s += "      }\n";
+    }
     // with `sync`, the threads of a group wait for each other after every
     // chunk (named barrier 1 + group of blockDim / T threads), so the warps of a
     // group run the same chunk's code together and share the instruction
@@ -634,7 +662,7 @@ std::string kernel_fn(const Builder& B, const Plan& pl, const std::vector<std::v
         std::string r;
         for (int c = pl.prog_first[prog]; c < pl.prog_first[prog] + pl.prog_count[prog]; ++c) {
             if (sync)
-                r += ind + "if (s.valid) ivb_ck" + S(c) + "(st, ss);\n" + ind + "asm volatile(\"bar.sync " + S(1 + g) +
+                r += ind + "if (s0.valid) ivb_ck" + S(c) + "(st, ss);\n" + ind + "asm volatile(\"bar.sync " + S(1 + g) +
                      ", %0;\" :: \"r\"(per) : \"memory\");\n";
             else r += ind + "ivb_ck" + S(c) + "(st, ss);\n";
         }
@@ -648,15 +676,17 @@ std::string kernel_fn(const Builder& B, const Plan& pl, const std::vector<std::v
         s += ind + (g ? "else if" : "if") + " (grp == " + S(g) + ") {\n";
         for (int o : groups[g]) {
             s += calls(p0 + o, g, ind + "  ");
-            const std::string in2 = ind + "  " + (sync ? "if (s.valid) " : "");
-            s += in2 + "{\n";
-            s += ind + "    F" + S(o) + " = st_ld(st, ss, " + S(slot_F(n, o)) + ");\n";
-            s += ind + "    if (excludes_feasible(" + S(B.P.out_kind[o]) + "u, F" + S(o) + ")) fl |= 1u;\n";
-            if (B.P.out_kind[o] == OUT_INEQ)
-                s += ind + "    if (!le0(st_ld(st, ss, " + S(slot_fc(n, o)) + ").hi)) fl |= 2u;\n";
-            if (o == obj) {
-                s += ind + "    obj_lo = F" + S(o) + ".lo;\n";
-                s += ind + "    fco = st_ld(st, ss, " + S(slot_fc(n, o)) + ").hi;\n";
+            s += ind + "  " + (sync ? "if (s0.valid) " : "") + "{\n";
+            for (int k = 0; k < K; ++k) {
+                const std::string Fk = "F" + S(o) + "_" + S(k), fl = "fl_" + S(k);
+                s += ind + "    " + Fk + " = st_ld(st, ss, " + S(slot_F(n, o) + k * ns) + ");\n";
+                s += ind + "    if (excludes_feasible(" + S(B.P.out_kind[o]) + "u, " + Fk + ")) " + fl + " |= 1u;\n";
+                if (B.P.out_kind[o] == OUT_INEQ)
+                    s += ind + "    if (!le0(st_ld(st, ss, " + S(slot_fc(n, o) + k * ns) + ").hi)) " + fl + " |= 2u;\n";
+                if (o == obj) {
+                    s += ind + "    obj_lo_" + S(k) + " = " + Fk + ".lo;\n";
+                    s += ind + "    fco_" + S(k) + " = st_ld(st, ss, " + S(slot_fc(n, o) + k * ns) + ").hi;\n";
+                }
             }
             s += ind + "  }\n";
         }
@@ -664,20 +694,29 @@ std::string kernel_fn(const Builder& B, const Plan& pl, const std::vector<std::v
     }
     if (!sync) s += "    }\n";
     if (T > 1) {
-        s += "    s_fl[threadIdx.x] = (unsigned char)fl;\n";
+        for (int k = 0; k < K; ++k) s += "    s_fl[" + S(k) + "][threadIdx.x] = (unsigned char)fl_" + S(k) + ";\n";
         s += "    __syncthreads();\n";
-        s += "    if (grp == " + S(gobj) + ") for (int h = 0; h < " + S(T) + "; ++h) fl |= s_fl[h * per + threadIdx.x % per];\n";
-        s += "    __syncthreads();\n";
+        s += "    if (grp == " + S(gobj) + ") for (int h = 0; h < " + S(T) + "; ++h) {\n";
+        for (int k = 0; k < K; ++k) s += "      fl_" + S(k) + " |= s_fl[" + S(k) + "][h * per + threadIdx.x % per];\n";
+        s += "    }\n    __syncthreads();\n";
     }
-    s += "    double ub = from_bits(0x7FF0000000000000LL);\n";
-    s += "    if (s.valid && grp == " + S(gobj) + ") {\n";
-    s += std::string("      if (") + (B.P.has_eq ? "false" : "!(fl & 2u)") + ") ub = fco;\n";
-    s += "      if (fl & 1u) obj_lo = from_bits(0x7FF0000000000000LL);\n";
-    s += "    }\n";
+    for (int k = 0; k < K; ++k) {
+        const std::string kk = S(k);
+        s += "    double ub_" + kk + " = from_bits(0x7FF0000000000000LL);\n";
+        s += "    if (" + sub(k) + ".valid && grp == " + S(gobj) + ") {\n";
+        s += std::string("      if (") + (B.P.has_eq ? "false" : "!(fl_" + kk + " & 2u)") + ") ub_" + kk + " = fco_" + kk +
+             ";\n";
+        s += "      if (fl_" + kk + " & 1u) obj_lo_" + kk + " = from_bits(0x7FF0000000000000LL);\n";
+        s += "    }\n";
+    }
     for (int g = 0; g < T; ++g) {
         s += std::string("    ") + (g ? "else if" : "if") + " (grp == " + S(g) + ") {\n";
-        for (int o : groups[g]) s += "      reduce_output(P, s, " + S(no) + ", " + S(o) + ", F" + S(o) + ");\n";
-        if (g == gobj) s += "      reduce_extras(P, s, " + S(no) + ", ub, obj_lo);\n";
+        for (int k = 0; k < K; ++k) {
+            for (int o : groups[g])
+                s += "      reduce_output(P, " + sub(k) + ", " + S(no) + ", " + S(o) + ", F" + S(o) + "_" + S(k) + ");\n";
+            if (g == gobj)
+                s += "      reduce_extras(P, " + sub(k) + ", " + S(no) + ", ub_" + S(k) + ", obj_lo_" + S(k) + ");\n";
+        }
         s += "    }\n";
     }
     s += "  });\n}\n";
@@ -782,7 +821,9 @@ SegSource jit_seg_source(const HostProgram& P, const std::vector<Ins>& ins, cons
     SegSource out;
     for (const Builder::Prog& pr : B.progs) {
         long long rec = 0;
-        std::vector<Chunk> ch = cut(B, pr.st, pol.chunk_cost, pol.chunk_stmts, B.nie_only ? 0 : pol.recompute, &rec);
+        const int copies = pol.ilp == 2 ? 2 : 1;
+        std::vector<Chunk> ch = cut(B, pr.st, pol.chunk_cost / copies, pol.chunk_stmts / copies,
+                                    B.nie_only ? 0 : pol.recompute, &rec);
         std::set<int> ends;
         if (pr.out < 0) {
             for (int o = 0; o < no; ++o) ends.insert(B.vid.at("fc" + S(o)));
@@ -797,7 +838,10 @@ SegSource jit_seg_source(const HostProgram& P, const std::vector<Ins>& ins, cons
         pl.chunks.insert(pl.chunks.end(), ch.begin(), ch.end());
         pl.recomputed += rec;
     }
-    out.state_units = 2 * std::max(pl.n_slots, 1);
+    const int K = pol.ilp == 2 ? 2 : 1;
+    const int ns = std::max(pl.n_slots, 1);
+    out.state_units = 2 * ns * K;
+    out.ilp = K;
     out.chunks = (int)pl.chunks.size();
     out.loads = pl.loads;
     out.stores = pl.stores;
@@ -811,9 +855,9 @@ SegSource jit_seg_source(const HostProgram& P, const std::vector<Ins>& ins, cons
         if (T > 1 && (B.shared_point || no < T || block_max < 32 * T)) continue;
         out.ts.push_back(T);
         const std::vector<std::vector<int>> groups = group_outputs(B, T);
-        k += kernel_fn(B, pl, groups, T, false, T == 1 ? "ivb_jit_bound" : "ivb_jit_bound_t" + S(T), block_max,
-                       min_blocks);
-        k += kernel_fn(B, pl, groups, T, true, "ivb_jit_bound_t" + S(T) + "_sync", block_max, min_blocks);
+        k += kernel_fn(B, pl, groups, T, false, K, ns, T == 1 ? "ivb_jit_bound" : "ivb_jit_bound_t" + S(T),
+                       block_max, min_blocks);
+        k += kernel_fn(B, pl, groups, T, true, K, ns, "ivb_jit_bound_t" + S(T) + "_sync", block_max, min_blocks);
     }
     out.kernel = k;
     // chunks spread over units of similar size, compiled in parallel
@@ -822,7 +866,7 @@ SegSource jit_seg_source(const HostProgram& P, const std::vector<Ins>& ins, cons
     for (int u = 0; u < U; ++u) {
         std::string src = unit_head(emulate, false);
         const int b = (int)((long long)C * u / U), e = (int)((long long)C * (u + 1) / U);
-        for (int c = b; c < e; ++c) src += chunk_fn(B, pl, c);
+        for (int c = b; c < e; ++c) src += chunk_fn(B, pl, c, K, ns);
         out.units.push_back(src);
     }
     return out;

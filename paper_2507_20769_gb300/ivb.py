@@ -37,7 +37,8 @@ class ivb_options(ctypes.Structure):
                 ("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("max_nodes", ctypes.c_int32), ("frame_in_shared", ctypes.c_int32), ("specialize", ctypes.c_int32),
                 ("emulate", ctypes.c_int32), ("recompute", ctypes.c_int32), ("seg_chunk", ctypes.c_int32),
-                ("seg_regs", ctypes.c_int32), ("threads_per_subdomain", ctypes.c_int32), ("seg_sync", ctypes.c_int32)]
+                ("seg_regs", ctypes.c_int32), ("threads_per_subdomain", ctypes.c_int32), ("seg_sync", ctypes.c_int32),
+                ("seg_ilp", ctypes.c_int32)]
 
 
 class ivb_tuning(ctypes.Structure):
@@ -105,7 +106,7 @@ def lib() -> ctypes.CDLL:
         L.ivb_propagate.argtypes = [P, I32, P, D, I32, P, P]
         L.ivb_host_gradient.argtypes = [P, P, I32, I32, P]
         L.ivb_specialize_compile.argtypes = [P, I32, I32, P, P, P]
-        L.ivb_get_segmentation.argtypes = [P, P, P, P, P, P, P]
+        L.ivb_get_segmentation.argtypes = [P, P, P, P, P, P, P, P]
         L.ivb_get_tuning_ex.argtypes = [P, P]
         for f in ("ivb_create_problem", "ivb_bound_nodes", "ivb_bound_nodes_ex", "ivb_enclose", "ivb_point_grad",
                   "ivb_pick_splits", "ivb_get_tuning", "ivb_bnb_solve", "ivb_op_counts", "ivb_fp64_probe",
@@ -440,12 +441,13 @@ class Problem:
                 "emulate": em.value}
 
     def ivb_get_segmentation(self) -> dict:
-        su, ch, rc = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        su, ch, rc, il = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         ld, stv, re = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         _check(lib().ivb_get_segmentation(self._h, ctypes.byref(su), ctypes.byref(ch), ctypes.byref(ld),
-                                          ctypes.byref(stv), ctypes.byref(re), ctypes.byref(rc)), self._h)
+                                          ctypes.byref(stv), ctypes.byref(re), ctypes.byref(rc), ctypes.byref(il)),
+               self._h)
         return {"state_units": su.value, "chunks": ch.value, "state_loads": ld.value, "state_stores": stv.value,
-                "recomputed": re.value, "recompute": rc.value}
+                "recomputed": re.value, "recompute": rc.value, "ilp": il.value}
 
     def ivb_op_counts(self) -> dict:
         c = (ctypes.c_int64 * 8)()

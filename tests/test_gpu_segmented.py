@@ -263,3 +263,38 @@ def test_bnb_split_target_picked_from_the_launch():
     assert tgt == 1 << 20 or tgt * 8 >= 4 * wave
     assert r2["split_target"] == 1000
     assert r["lb"] <= r["ub"] and r2["lb"] <= r2["ub"]
+
+
+# ------------------------------------ two subdomains per thread (seg_ilp = 2)
+
+@pytest.mark.parametrize("path", ["graph", "plain"])
+@pytest.mark.parametrize("tpsub", [1, 2])
+@pytest.mark.parametrize("recompute", [0, 1])
+def test_two_subdomains_per_thread_bit_exact_rational(path, tpsub, recompute):
+    """every statement run on two subdomains at once (the second copy repeats
+    the first where the index range ends): the ragged batch's results equal
+    the oracle's bit for bit"""
+    t = rational_problem(n=3, K=50, n_ineq=3)
+    boxes, splits = ragged_batch(t, 37, seed=17)
+    opts = dict(grad_mode="adjoint", specialize=3, seg_ilp=2, threads_per_subdomain=tpsub, recompute=recompute,
+                seg_chunk=24, use_graph=int(path == "graph"), batched=int(path != "plain"))
+    with ivb.Problem(t, **opts) as p:
+        assert p.get_segmentation()["ilp"] == 2
+        r = p.bound_nodes_ex(boxes, splits, want_hull=True)
+        tun = p.get_tuning()
+        assert tun["subdomains_per_pass"] == 2 * tun["block_threads"] // tun["threads_per_subdomain"]
+    ref = oracle.bound_nodes(t, boxes, splits, grad_mode="adjoint", tight=True)
+    for k in ("lb", "ub", "minlo", "maxhi"):
+        assert np.array_equal(r[k], ref[k]), k
+    assert np.array_equal(r["infeasible"].astype(bool), ref["infeasible"])
+
+
+@pytest.mark.parametrize("form", ["mvf", "mvf_nie"])
+@pytest.mark.parametrize("sync", [0, 1])
+def test_two_subdomains_per_thread_identical_to_interpreter(form, sync):
+    """configuration 2 (exp/log tape), both chunk synchronisation variants"""
+    t = W.config_tape(2)
+    boxes, splits = ragged_batch(t, 23, seed=5)
+    a, b = bound_seg_and_interp(t, boxes, splits, dict(seg_ilp=2, seg_sync=sync), form=form)
+    for k in KEYS:
+        assert same_bits(a[k], b[k]), k
