@@ -74,8 +74,8 @@ MUTANTS = [
      "            if (out_kind[q] == KIND_INEQ && minlo[q] > 0.0) inf = 1;",
      "            if (out_kind[q] == KIND_INEQ && maxhi[q] > 0.0) inf = 1;"),
     ("tight exp widens its lower end the wrong way",
-     "    if (tight) { qreal q = Q_EXP((qreal)x); r = q_to_dn(q - q * Q_EPS); }",
-     "    if (tight) { qreal q = Q_EXP((qreal)x); r = q_to_up(q + q * Q_EPS); }"),
+     "    if (tight) { qreal q = Q_EXP((qreal)x); r = q_to_dn(q - q * Q_EPS); if (tight > 1)",
+     "    if (tight) { qreal q = Q_EXP((qreal)x); r = q_to_up(q + q * Q_EPS); if (tight > 1)"),
     ("square root rounds its lower end upward",
      "static double sqrt_dn(double x) {\n    volatile double vx = x, r;\n    fesetround(FE_DOWNWARD);",
      "static double sqrt_dn(double x) {\n    volatile double vx = x, r;\n    fesetround(FE_UPWARD);"),
