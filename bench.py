@@ -60,11 +60,16 @@ def parse():
                     help="bounding kernel: -1 the library's choice (segmented for these tapes), 0 interpreter, "
                          "1 compact, 3 segmented")
     ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end measurement")
+    ap.add_argument("--block-threads", type=int, default=0,
+                    help="fixed launch of the headline problem (threads per block; 0: autotuned)")
+    ap.add_argument("--blocks-per-sm", type=int, default=0, help="fixed blocks per SM (0: autotuned)")
+    ap.add_argument("--seg-sync", type=int, default=-1,
+                    help="segmented kernel's chunk synchronisation (-1: autotuned, 0 or 1 fixed)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target oracle sample time")
     ap.add_argument("--bnb", type=int, default=1, help="B&B time-to-gap comparisons (rank 0)")
     ap.add_argument("--bnb-configs", type=str, default="1,2,3,5", help="configurations of the B&B comparison")
-    ap.add_argument("--bnb-cap", type=float, default=20.0, help="time cap per B&B run, seconds")
-    ap.add_argument("--bnb-cap5", type=float, default=30.0, help="time cap per B&B run on configuration 5")
+    ap.add_argument("--bnb-cap", type=float, default=15.0, help="time cap per B&B run, seconds")
+    ap.add_argument("--bnb-cap5", type=float, default=20.0, help="time cap per B&B run on configuration 5")
     ap.add_argument("--oracle-bnb", type=float, default=15.0,
                     help="time cap of the oracle-backed B&B on configurations 1 and 2 (0: skip)")
     ap.add_argument("--secondary", type=int, default=1, help="also time the configuration-2 step")
@@ -254,7 +259,8 @@ def main():
     units_step = subs_step * t.n_out
     t0 = time.perf_counter()
     p = ivb.Problem(t, grad_mode="adjoint", batched=1, use_graph=1, autotune=1, specialize=args.specialize,
-                    max_nodes=max(64, n_nodes))
+                    max_nodes=max(64, n_nodes), block_threads=args.block_threads, blocks_per_sm=args.blocks_per_sm,
+                    seg_sync=args.seg_sync)
     create_s = time.perf_counter() - t0
     boxes_d = torch.from_numpy(boxes).to(dev)
     splits_d = torch.from_numpy(splits).to(dev)

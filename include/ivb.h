@@ -166,6 +166,11 @@ typedef struct {
                                   1 or 2 (two independent dependency chains
                                   per thread, every statement run on both
                                   interleaved); 0 (default): 1              */
+    int32_t seg_outline;       /* segmented kernel: 1 calls + - * sqr and the
+                                  fused accumulation out of line (a third of
+                                  the code every warp streams through, a call
+                                  per statement); 0 inlines them; -1
+                                  (default): the library's choice, now 1    */
 } ivb_options;
 
 typedef struct ivb_problem ivb_problem;

@@ -513,6 +513,32 @@ std::string plan_prog(const Builder& B, const std::vector<Chunk>& ch, const std:
     return "";
 }
 
+// out-of-line copies of the short interval operations (option seg_outline):
+// a statement then compiles to a call instead of the operation's selects and
+// directed multiplies, which shrinks the code every warp streams through
+const char* kOutline =
+    "namespace ivb {\n"
+    "static __device__ __noinline__ iv o_add(iv a, iv b) { return iv_add(a, b); }\n"
+    "static __device__ __noinline__ iv o_sub(iv a, iv b) { return iv_sub(a, b); }\n"
+    "static __device__ __noinline__ iv o_mul(iv a, iv b) { return iv_mul(a, b); }\n"
+    "static __device__ __noinline__ iv o_sqr(iv a) { return iv_sqr(a); }\n"
+    "static __device__ __noinline__ iv o_fma(iv a, iv b, iv c) { return iv_fma(a, b, c); }\n"
+    "}\n";
+
+// the statement's code with the short operations called out of line
+std::string outline_code(const std::string& code) {
+    std::string r = code;
+    for (const char* f : {"iv_add(", "iv_sub(", "iv_mul(", "iv_sqr(", "iv_fma("}) {
+        const std::string from = f, to = std::string("o_") + (f + 3);
+        size_t at = 0;
+        while ((at = r.find(from, at)) != std::string::npos) {
+            r.replace(at, from.size(), to);
+            at += to.size();
+        }
+    }
+    return r;
+}
+
 // a statement's code for copy k of K (variable names end in '$')
 std::string copy_code(const std::string& code, int K, int k) {
     const std::string sfx = K > 1 ? "_" + S(k) : "";
@@ -528,7 +554,7 @@ std::string copy_code(const std::string& code, int K, int k) {
 // C++ of one chunk function. With K = 2 every statement runs twice, on two
 // subdomains, interleaved: two independent dependency chains per thread.
 // Copy k keeps its values in state slots offset by k * ns.
-std::string chunk_fn(const Builder& B, const Plan& pl, int c, int K, int ns) {
+std::string chunk_fn(const Builder& B, const Plan& pl, int c, int K, int ns, bool outline) {
     const Chunk& ch = pl.chunks[c];
     const std::map<int, int>& ld = pl.load_slot[c];
     const std::map<int, int>& stv = pl.store_slot[c];
@@ -566,7 +592,7 @@ std::string chunk_fn(const Builder& B, const Plan& pl, int c, int K, int ns) {
                 }
                 loaded.insert(v);
             }
-        for (int k = 0; k < K; ++k) s += "  " + copy_code(t.code, K, k) + "\n";
+        for (int k = 0; k < K; ++k) s += "  " + copy_code(outline ? outline_code(t.code) : t.code, K, k) + "\n";
         for (int v : t.writes) written.insert(v);
         for (int v : t.writes) {
             auto it = stv.find(v);
@@ -865,8 +891,9 @@ SegSource jit_seg_source(const HostProgram& P, const std::vector<Ins>& ins, cons
     const int U = std::max(1, std::min(C, pol.units));
     for (int u = 0; u < U; ++u) {
         std::string src = unit_head(emulate, false);
+        if (pol.outline) src += kOutline;
         const int b = (int)((long long)C * u / U), e = (int)((long long)C * (u + 1) / U);
-        for (int c = b; c < e; ++c) src += chunk_fn(B, pl, c, K, ns);
+        for (int c = b; c < e; ++c) src += chunk_fn(B, pl, c, K, ns, pol.outline);
         out.units.push_back(src);
     }
     return out;

@@ -38,7 +38,7 @@ class ivb_options(ctypes.Structure):
                 ("max_nodes", ctypes.c_int32), ("frame_in_shared", ctypes.c_int32), ("specialize", ctypes.c_int32),
                 ("emulate", ctypes.c_int32), ("recompute", ctypes.c_int32), ("seg_chunk", ctypes.c_int32),
                 ("seg_regs", ctypes.c_int32), ("threads_per_subdomain", ctypes.c_int32), ("seg_sync", ctypes.c_int32),
-                ("seg_ilp", ctypes.c_int32)]
+                ("seg_ilp", ctypes.c_int32), ("seg_outline", ctypes.c_int32)]
 
 
 class ivb_tuning(ctypes.Structure):

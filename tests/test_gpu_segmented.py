@@ -298,3 +298,25 @@ def test_two_subdomains_per_thread_identical_to_interpreter(form, sync):
     a, b = bound_seg_and_interp(t, boxes, splits, dict(seg_ilp=2, seg_sync=sync), form=form)
     for k in KEYS:
         assert same_bits(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("recompute", [0, 1])
+@pytest.mark.parametrize("tpsub", [1, 2])
+def test_inlined_short_operations_bit_exact(recompute, tpsub):
+    """seg_outline = 0 (+ - * sqr and the fused accumulation inlined instead
+    of called out of line, the default): the oracle's bits on a rational
+    tape, the interpreter's on configuration 2"""
+    t = rational_problem(n=3, K=50, n_ineq=3)
+    boxes, splits = ragged_batch(t, 29, seed=19)
+    with ivb.Problem(t, specialize=3, seg_outline=0, recompute=recompute, threads_per_subdomain=tpsub,
+                     seg_chunk=40) as p:
+        r = p.bound_nodes_ex(boxes, splits, want_hull=True)
+    ref = oracle.bound_nodes(t, boxes, splits, grad_mode="adjoint", tight=True)
+    for k in ("lb", "ub", "minlo", "maxhi"):
+        assert np.array_equal(r[k], ref[k]), k
+    t2 = W.config_tape(2)
+    boxes, splits = ragged_batch(t2, 17, seed=6)
+    a, b = bound_seg_and_interp(t2, boxes, splits, dict(seg_outline=0, recompute=recompute,
+                                                        threads_per_subdomain=tpsub))
+    for k in KEYS:
+        assert same_bits(a[k], b[k]), k
