@@ -332,8 +332,7 @@ def main():
                                           f"({secs:.1f} s; adjoint gradients, fast exp/log mode); the reduction "
                                           "of Step 3 is a min over them",
                                 "value_1core": rate1, "cpu": cpu_model()}
-        if p.get_specialization()["active"]:
-            line["interpreter"] = interpreter_compare(t, boxes_d, splits_d, out, flush, stream, subs_step, step_s)
+        line["kernels"] = kernel_compare(t, boxes_d, splits_d, out, flush, stream, subs_step, step_s, dev)
     p.destroy()
     if rank == 0 and world == 1 and args.secondary:
         line["config2"] = config2_step(dev, flush, stream)
@@ -371,7 +370,7 @@ def roofline_block(p, subs_step, step_s, clk, dev, probes=False):
     ops_per_sub = sum(counts.values())
     achieved = ops_per_sub * subs_step / step_s
     seg = p.get_segmentation()
-    which = "segmented" if seg["chunks"] else ("specialised" if p.get_specialization()["active"] else "interpreter")
+    which = {0: "interpreter", 1: "specialised", 2: "segmented"}[p.get_tuning()["kernel"]]
     rf = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "G FP64 endpoint-op/s",
           "frac": achieved / peak, "traffic": traffic_for(subs_step, which),
           "peak_source": f"derived: {sms} SMs x 2 FP64 lanes/clock x {clock_mhz:.0f} MHz (SM clock sampled during "
@@ -400,8 +399,9 @@ def roofline_block(p, subs_step, step_s, clk, dev, probes=False):
 def kernel_desc(p, create_s=None):
     s = p.get_specialization()
     d = {"problem_create_seconds": round(create_s, 2)} if create_s is not None else {}
-    if not s["active"]:
-        d["bounding_kernel"] = "tape interpreter (ivb::k_bound)"
+    if not s["active"] or p.get_tuning()["kernel"] == 0:
+        d["bounding_kernel"] = "tape interpreter (ivb::k_bound)" + (
+            " (the autotuner timed it faster than the compiled kernel)" if s["active"] else "")
         return d
     seg = p.get_segmentation()
     d.update({"bounding_kernel": ("segmented " if seg["chunks"] else "") +
@@ -413,28 +413,35 @@ def kernel_desc(p, create_s=None):
     return d
 
 
-def interpreter_compare(t, boxes_d, splits_d, out, flush, stream, subs_step, step_s):
-    """the same step through the tape interpreter (bit-identical bounds), for context"""
+def kernel_compare(t, boxes_d, splits_d, out, flush, stream, subs_step, step_s, dev):
+    """the same step through each kernel on its own (bit-identical bounds):
+    the tape interpreter, and the segmented tape-specialised kernel with its
+    reverse-segment recomputation (policy 1) -- the two the library's
+    autotuner chooses between for these tapes"""
     import torch
     from paper_2507_20769_gb300 import ivb
-    p = ivb.Problem(t, grad_mode="adjoint", batched=1, use_graph=1, autotune=1, specialize=0,
-                    max_nodes=max(64, int(boxes_d.shape[0])))
-    for _ in range(2):
-        p.bound_nodes_ex(boxes_d, splits_d, out=out)
-    ms = []
-    for _ in range(2):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        p.bound_nodes_ex(boxes_d, splits_d, out=out)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms.append(a.elapsed_time(b))
-    tun = p.get_tuning()
-    p.destroy()
-    m = float(np.median(ms))
-    return {"ms_per_step": m, "subdomains_per_s": subs_step / (m / 1e3),
-            "specialised_speedup": m / (1e3 * step_s), "tuning": tun}
+    res = {}
+    for name, spec in (("interpreter", 0), ("segmented", 3)):
+        p = ivb.Problem(t, grad_mode="adjoint", batched=1, use_graph=1, autotune=1, specialize=spec,
+                        max_nodes=max(64, int(boxes_d.shape[0])))
+        for _ in range(2):
+            p.bound_nodes_ex(boxes_d, splits_d, out=out)
+        ms = []
+        for _ in range(3):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            p.bound_nodes_ex(boxes_d, splits_d, out=out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        m = float(np.median(ms))
+        rf = roofline_block(p, subs_step, m / 1e3, {"sm_mhz": None}, dev)
+        res[name] = {"ms_per_step": m, "subdomain_bounds_per_s": subs_step * t.n_out / (m / 1e3),
+                     "frac": rf["frac"], "traffic": rf["traffic"], "tuning": p.get_tuning(),
+                     "kernel": kernel_desc(p), "vs_headline": (1e3 * step_s) / m}
+        p.destroy()
+    return res
 
 
 def config2_step(dev, flush, stream, steps=5):

@@ -129,7 +129,8 @@ typedef struct {
                                   the tape has at most 1024 interval
                                   operations per subdomain, else as 3 in
                                   adjoint mode and the interpreter in forward
-                                  mode                                      */
+                                  mode, and the autotuner keeps the
+                                  interpreter instead when it times faster  */
     int32_t emulate;           /* tape-specialised kernel only: endpoint
                                   operations computed by an exact emulation
                                   on the integer pipes (bit-identical to the
@@ -369,6 +370,12 @@ typedef struct {
     int32_t subdomains_per_pass;   /* block_threads / threads_per_subdomain x
                                       subdomains per thread                     */
     int32_t chunk_sync;            /* segmented kernel: groups kept on one chunk */
+    int32_t kernel;                /* the reduce kernel the launches use: 0 the
+                                      tape interpreter, 1 the tape-specialised
+                                      kernel, 2 the segmented one (with
+                                      specialize = -1 the autotuner times the
+                                      interpreter beside the compiled kernel and
+                                      keeps the faster)                          */
     int32_t candidates;            /* launch configurations timed (0: none)      */
     float best_ms, worst_ms;       /* their times on the tuning sample           */
 } ivb_tuning;

@@ -63,11 +63,15 @@ int frame_units(const ivb_problem* p) {
 
 bool use_jit(const ivb_problem* p) { return p->jit.kern != nullptr; }
 
+// the reduce launches run the tape-specialised kernel (loaded, and not
+// outtimed by the interpreter in the autotuner)
+bool reduce_jit(const ivb_problem* p) { return use_jit(p) && !p->tuned_interp; }
+
 // per-thread units of device memory the reduce kernel needs: the interpreter's
 // frame, a segmented kernel's state area, nothing for the other specialised
 // kernels (registers only)
 int reduce_units(const ivb_problem* p) {
-    if (!use_jit(p)) return frame_units(p);
+    if (!reduce_jit(p)) return frame_units(p);
     return p->jit.state_units;
 }
 
@@ -177,13 +181,13 @@ size_t smem_bytes(const ivb_problem* p, int block, int frame_smem) {
 // the reduce-mode bounding kernel: tape-specialised when compiled, else the interpreter
 cudaError_t launch_reduce(ivb_problem* p, const KParams& K, int grid, int block, int frame_smem, cudaStream_t s,
                           int tpsub, bool sync) {
-    if (use_jit(p)) return jit_launch(p->jit, K, grid, block, s, tpsub, sync);
+    if (reduce_jit(p)) return jit_launch(p->jit, K, grid, block, s, tpsub, sync);
     return launch_bound(kernel_mode(p, false), K, grid, block, smem_bytes(p, block, frame_smem), s);
 }
 
 // resident blocks per SM of the reduce kernel
 int reduce_occupancy(ivb_problem* p, int block, int frame_smem, int tpsub = 1, bool sync = false) {
-    if (use_jit(p)) return block <= p->jit.max_threads ? jit_occupancy(p->jit, block, tpsub, sync) : 0;
+    if (reduce_jit(p)) return block <= p->jit.max_threads ? jit_occupancy(p->jit, block, tpsub, sync) : 0;
     return occupancy_blocks(kernel_mode(p, false), block, smem_bytes(p, block, frame_smem));
 }
 
@@ -215,19 +219,19 @@ ivb_status enqueue_bound(ivb_problem* p, int grid, int block, int tile, int fram
 
 struct TuneCand {
     int block, bps, smem, tpsub, tile_mult;
-    bool sync;
+    bool sync, interp;
 };
 
 // subdomains a block covers per pass of its tile loop
 int pass_size(const ivb_problem* p, int block, int tpsub) {
-    const int ilp = use_jit(p) && p->jit.state_units > 0 ? p->jit.ilp : 1;
+    const int ilp = reduce_jit(p) && p->jit.state_units > 0 ? p->jit.ilp : 1;
     return block / std::max(1, tpsub) * ilp;
 }
 
 // threads-per-subdomain values the loaded kernel offers (1 unless segmented)
 std::vector<int> tpsub_choices(const ivb_problem* p) {
     std::vector<int> v{1};
-    if (use_jit(p))
+    if (reduce_jit(p))
         for (int t : {2, 4})
             if (p->jit.kern_t[tpsub_index(t)] && (p->opt.threads_per_subdomain == 0 || p->opt.threads_per_subdomain == t))
                 v.push_back(t);
@@ -237,7 +241,7 @@ std::vector<int> tpsub_choices(const ivb_problem* p) {
 
 // chunk synchronisation choices: the segmented kernels come with and without
 std::vector<bool> sync_choices(const ivb_problem* p) {
-    if (!use_jit(p) || !p->jit.kern_sync[0]) return {false};
+    if (!reduce_jit(p) || !p->jit.kern_sync[0]) return {false};
     if (p->opt.seg_sync == 0) return {false};
     if (p->opt.seg_sync == 1) return {true};
     return {false, true};
@@ -255,6 +259,13 @@ ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
     const int blocks[] = {64, 128, 256};
     const int bpss[] = {1, 2, 3, 4, 6, 8};
     int max_threads = 0;
+    // with the library's choice of kernel, the interpreter competes with the
+    // tape-specialised kernel; candidates are generated (and timed) with the
+    // problem switched to the kernel they use
+    std::vector<bool> kernels{false};
+    if (use_jit(p) && p->opt.specialize == -1) kernels.push_back(true);
+    for (bool ip : kernels) {
+    p->tuned_interp = ip;
     for (bool sy : sync_choices(p))
     for (int t : tpsub_choices(p))
         for (int b : blocks)
@@ -263,15 +274,17 @@ ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
                 if (warps < 4 || warps > 32 || b < 32 * t) continue;
                 for (int sm = 0; sm < 2; ++sm) {
                     const size_t bytes = smem_bytes(p, b, sm);
-                    if (sm && (use_jit(p) || bytes + 1024 > (size_t)p->smem_optin || bytes * k > 220 * 1024)) continue;
+                    if (sm && (reduce_jit(p) || bytes + 1024 > (size_t)p->smem_optin || bytes * k > 220 * 1024)) continue;
                     if (p->opt.frame_in_shared == 0 && sm) continue;
-                    if (p->opt.frame_in_shared == 1 && !sm && !use_jit(p)) continue;
+                    if (p->opt.frame_in_shared == 1 && !sm && !reduce_jit(p)) continue;
                     if (reduce_occupancy(p, b, sm, t, sy) < k) continue;
-                    cands.push_back({b, k, sm, t, 1, sy});
+                    cands.push_back({b, k, sm, t, 1, sy, ip});
                     max_threads = std::max(max_threads, b * k * p->sm_count);
                 }
             }
-    if (cands.empty()) cands.push_back({64, 1, 0, 1, 1, false});
+    }
+    p->tuned_interp = false;
+    if (cands.empty()) cands.push_back({64, 1, 0, 1, 1, false, false});
     // time only [0, cap) of the global index range
     const long long cap = std::min<long long>(total, std::max<long long>(4LL * max_threads, 1LL << 18));
     long long* hdr = reinterpret_cast<long long*>(p->h_queue);
@@ -288,6 +301,7 @@ ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
     int timed = 0;
     auto time_one = [&](const TuneCand& c) -> ivb_status {
         const int grid = p->sm_count * c.bps;
+        p->tuned_interp = c.interp;
         ivb_status r = IVB_OK;
         if (reduce_units(p) > 0) r = ensure_frame(p, grid, c.block, reduce_units(p));
         if (r) return r;
@@ -319,6 +333,7 @@ ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
             if (st) break;
         }
     }
+    p->tuned_interp = false;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     // restore the batch's index range
@@ -331,6 +346,7 @@ ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
     p->frame_smem = bc.smem;
     p->tpsub = bc.tpsub;
     p->chunk_sync = bc.sync;
+    p->tuned_interp = bc.interp;
     p->tile = bc.tile_mult * pass_size(p, bc.block, bc.tpsub);
     p->tune_candidates = timed;
     p->tune_best_ms = best;
@@ -345,7 +361,7 @@ ivb_status default_tuning(ivb_problem* p) {
     p->block = p->opt.block_threads > 0 ? p->opt.block_threads : 128;
     p->bps = p->opt.blocks_per_sm > 0 ? p->opt.blocks_per_sm : 4;
     const size_t bytes = smem_bytes(p, p->block, 1);
-    if (use_jit(p)) p->frame_smem = 0;   // frames serve only the interpreter's store mode
+    if (reduce_jit(p)) p->frame_smem = 0;   // frames serve only the interpreter's store mode
     else if (p->opt.frame_in_shared == 1) p->frame_smem = 1;
     else if (p->opt.frame_in_shared == 0) p->frame_smem = 0;
     else p->frame_smem = (bytes + 1024 <= (size_t)p->smem_optin && bytes * p->bps <= 220 * 1024) ? 1 : 0;
@@ -905,6 +921,7 @@ extern "C" ivb_status ivb_get_tuning_ex(ivb_problem* p, ivb_tuning* t) {
     t->frame_in_shared = p->frame_smem;
     t->threads_per_subdomain = p->tpsub;
     t->chunk_sync = p->chunk_sync ? 1 : 0;
+    t->kernel = reduce_jit(p) ? (p->jit.state_units > 0 ? 2 : 1) : 0;
     t->subdomains_per_pass = pass_size(p, p->block, p->tpsub);
     t->candidates = p->tune_candidates;
     t->best_ms = p->tune_best_ms;

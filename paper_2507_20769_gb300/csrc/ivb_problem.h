@@ -44,6 +44,7 @@ struct ivb_problem {
     int block = 128, bps = 4, tile = 512, frame_smem = 0;
     int tpsub = 1;            // threads per subdomain (segmented kernel: 1, 2 or 4)
     bool chunk_sync = false;  // segmented kernel: a group's warps kept on the same chunk
+    bool tuned_interp = false;  // the autotuner chose the interpreter over the specialised kernel
     int tune_candidates = 0;  // launch configurations the autotuner timed
     float tune_best_ms = 0.f, tune_worst_ms = 0.f;
     // graph of the batched call

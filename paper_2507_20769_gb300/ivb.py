@@ -44,7 +44,8 @@ class ivb_options(ctypes.Structure):
 class ivb_tuning(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("frame_in_shared", ctypes.c_int32), ("threads_per_subdomain", ctypes.c_int32),
-                ("subdomains_per_pass", ctypes.c_int32), ("chunk_sync", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("subdomains_per_pass", ctypes.c_int32), ("chunk_sync", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("candidates", ctypes.c_int32),
                 ("best_ms", ctypes.c_float), ("worst_ms", ctypes.c_float)]
 
 

@@ -41,7 +41,7 @@ def test_library_exports_every_declared_function(lib):
 def test_struct_sizes_match_header(lib):
     assert W.IVB_OP_DTYPE.itemsize == 24
     assert ctypes.sizeof(ivb.ivb_options) == 20 * 4
-    assert ctypes.sizeof(ivb.ivb_tuning) == 10 * 4
+    assert ctypes.sizeof(ivb.ivb_tuning) == 11 * 4
     o = ivb.ivb_options_default()
     assert (o.grad_mode, o.form, o.batched, o.use_graph, o.max_nodes, o.specialize, o.emulate) == (1, 0, 1, 1, 4096, 0, -1)
     assert (o.recompute, o.seg_chunk, o.seg_regs, o.threads_per_subdomain, o.seg_sync, o.seg_ilp,

@@ -157,6 +157,8 @@ def test_segmented_full_scale_config5_identical_to_interpreter():
             if spec == -1:
                 assert p.get_segmentation()["chunks"] > 50
             res.append(p.bound_nodes_ex(boxes, splits, want_hull=True))
+            # with the library's choice the autotuner keeps whichever kernel timed faster
+            assert p.get_tuning()["kernel"] in ((0,) if spec == 0 else (0, 2))
     for k in KEYS:
         assert same_bits(res[0][k], res[1][k]), k
 
@@ -240,6 +242,7 @@ def test_autotuner_full_size_choice_reported_and_identical():
             out.append(p.bound_nodes_ex(boxes, splits, want_hull=True))
             tun = p.get_tuning()
         if spec == 3:
+            assert tun["kernel"] == 2    # an explicit segmented kernel is never replaced
             assert tun["candidates"] > 10 and tun["threads_per_subdomain"] in (1, 2, 4)
             assert tun["tile"] % tun["subdomains_per_pass"] == 0
             assert tun["subdomains_per_pass"] * tun["threads_per_subdomain"] == tun["block_threads"]
@@ -320,3 +323,24 @@ def test_inlined_short_operations_bit_exact(recompute, tpsub):
                                                         threads_per_subdomain=tpsub))
     for k in KEYS:
         assert same_bits(a[k], b[k]), k
+
+
+def test_library_choice_times_the_interpreter_beside_the_specialised_kernel():
+    """specialize = -1 on a large adjoint tape: the autotuner times the
+    interpreter's launch shapes beside the segmented kernel's and keeps the
+    faster; either way the bounds are the interpreter's bits, on the graph
+    and on later calls"""
+    t = W.config_tape(4)
+    boxes = W.bisection_frontier(t.root_box, 4, seed=3)
+    splits = np.tile(W.config_workload(4).splits, (4, 1)).astype(np.int32)
+    with ivb.Problem(t, grad_mode="adjoint", specialize=0) as p:
+        ref = p.bound_nodes_ex(boxes, splits, want_hull=True)
+    with ivb.Problem(t, grad_mode="adjoint", specialize=-1) as p:
+        assert p.get_specialization()["active"]
+        r1 = p.bound_nodes_ex(boxes, splits, want_hull=True)
+        tun = p.get_tuning()
+        r2 = p.bound_nodes_ex(boxes, splits, want_hull=True)
+    assert tun["kernel"] in (0, 2) and tun["candidates"] > 20
+    for r in (r1, r2):
+        for k in KEYS:
+            assert same_bits(ref[k], r[k]), k
