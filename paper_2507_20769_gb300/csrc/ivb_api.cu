@@ -250,8 +250,9 @@ std::vector<bool> sync_choices(const ivb_problem* p) {
 // Pick block size, blocks per SM, frame placement, threads per subdomain and
 // subdomains per grab (tile) by timing the bound kernel on the first
 // subdomains of the staged batch (results do not depend on the choice). The
-// timed index range is capped at a few waves of the widest candidate grid so
-// that tuning stays a small fraction of one call. Stage 1 times every
+// timed index range is capped at two waves of the widest candidate grid, and a
+// candidate whose warm-up is already far slower than the best is not timed
+// again, so that tuning stays a small fraction of a few calls. Stage 1 times every
 // (threads per subdomain, block, blocks per SM, frame placement); stage 2
 // times larger grabs (4 and 16 passes per grab) for the best of stage 1.
 ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
@@ -285,14 +286,15 @@ ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
     }
     p->tuned_interp = false;
     if (cands.empty()) cands.push_back({64, 1, 0, 1, 1, false, false});
-    // time only [0, cap) of the global index range
-    const long long cap = std::min<long long>(total, std::max<long long>(4LL * max_threads, 1LL << 18));
+    // time only [0, cap) of the global index range: two waves of the widest candidate grid
+    const long long cap = std::min<long long>(total, std::max<long long>(2LL * max_threads, 1LL << 18));
     long long* hdr = reinterpret_cast<long long*>(p->h_queue);
     const long long g_end = hdr[1];
     CK(cudaEventSynchronize(p->queue_free));
     hdr[1] = cap;
     CK(cudaMemcpyAsync(p->d_queue, p->h_queue, 16, cudaMemcpyHostToDevice, s));
-    cudaEvent_t e0, e1;
+    cudaEvent_t ew, e0, e1;
+    CK(cudaEventCreate(&ew));
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 1e30f, worst = 0.f;
@@ -306,15 +308,22 @@ ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
         if (reduce_units(p) > 0) r = ensure_frame(p, grid, c.block, reduce_units(p));
         if (r) return r;
         const int tile = c.tile_mult * pass_size(p, c.block, c.tpsub);
-        for (int rep = 0; rep < 2; ++rep) {      // warm-up, then timed
-            if (rep == 1) { cudaError_t ce = cudaEventRecord(e0, s); if (ce) return cuda_fail(p, ce, "event"); }
+        // warm-up run, timed too: a candidate whose warm-up already takes 1.5x the
+        // best time so far is not run again (its warm-up time stands)
+        CK(cudaEventRecord(ew, s));
+        r = enqueue_bound(p, grid, c.block, tile, c.smem, p->max_nodes, s, c.tpsub, c.sync);
+        if (r) return r;
+        CK(cudaEventRecord(e0, s));
+        CK(cudaEventSynchronize(e0));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, ew, e0));
+        if (!(best < 1e29f && ms > 1.5f * best)) {
             r = enqueue_bound(p, grid, c.block, tile, c.smem, p->max_nodes, s, c.tpsub, c.sync);
             if (r) return r;
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            CK(cudaEventElapsedTime(&ms, e0, e1));
         }
-        CK(cudaEventRecord(e1, s));
-        CK(cudaEventSynchronize(e1));
-        float ms = 0;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
         ++timed;
         worst = std::max(worst, ms);
         if (ms < best) { best = ms; bc = c; }
@@ -334,6 +343,7 @@ ivb_status autotune(ivb_problem* p, long long total, cudaStream_t s) {
         }
     }
     p->tuned_interp = false;
+    cudaEventDestroy(ew);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     // restore the batch's index range
