@@ -165,8 +165,14 @@ typedef struct {
                                   autotuner                                  */
     int32_t seg_ilp;           /* segmented kernel: subdomains per thread,
                                   1 or 2 (two independent dependency chains
-                                  per thread, every statement run on both
-                                  interleaved); 0 (default): 1              */
+                                  per thread, every statement run on both,
+                                  interleaved). With 2, the short operations
+                                  out of line and an `emulate` policy, the
+                                  two subdomains run in pairs instead: one
+                                  call per operation computes both, the
+                                  first on the FP64 pipe, the second's short
+                                  operations under the policy on the integer
+                                  pipes (dual-pipe). 0 (default): 1        */
     int32_t seg_outline;       /* segmented kernel: 1 calls + - * sqr and the
                                   fused accumulation out of line (a third of
                                   the code every warp streams through, a call
@@ -400,9 +406,10 @@ ivb_status ivb_get_segmentation(ivb_problem* p, int32_t* state_units, int32_t* c
 /* Generate and compile (NVRTC, sm_103a) the tape-specialised kernel of a
  * tape without loading it -- needs no GPU; compact = 1 as for specialize = 1,
  * 0 as for specialize = 2, 3 as for specialize = 3 (segmented, adjoint mode
- * only, default segmentation options). Reports ptxas' registers per thread
- * (the largest over the functions compiled) and spill-store bytes (summed),
- * and the compile time (each may be NULL).
+ * only, default segmentation options), 4 as 3 with seg_ilp = 2 and emulate =
+ * 15 (the paired dual-pipe form). Reports
+ * ptxas' registers per thread (the largest over the functions compiled) and
+ * spill-store bytes (summed), and the compile time (each may be NULL).
  * IVB_ETAPE for an invalid tape, IVB_ENOTSUP (message in ivb_last_error(NULL))
  * when the program does not compile. */
 ivb_status ivb_specialize_compile(const ivb_tape* tape, int32_t grad_mode, int32_t compact, int32_t* registers,

@@ -981,14 +981,15 @@ extern "C" ivb_status ivb_specialize_compile(const ivb_tape* tape, int32_t grad_
     std::vector<char> cubin;
     std::string tables;
     int regs = 0, spill = 0;
-    if (compact == 3) {
+    if (compact == 3 || compact == 4) {
         if (grad_mode != IVB_GRAD_ADJOINT)
             return fail(nullptr, IVB_EINVAL, "the segmented kernel needs grad_mode IVB_GRAD_ADJOINT");
         ivb_options o;
         ivb_options_default(&o);
+        if (compact == 4) o.seg_ilp = 2;
         const SegPolicy pol = seg_policy(o);
         const SegSource src = jit_seg_source(P, ins, rins, consts, kJitBlockMax, seg_min_blocks(pol.max_regs),
-                                             kJitDefaultEmulate, 0, pol);
+                                             compact == 4 ? 15 : kJitDefaultEmulate, 0, pol);
         e = jit_seg_compile(src, pol.max_regs, cubin, tables, seconds, &regs, &spill);
     } else {
         const std::string src =

@@ -190,7 +190,7 @@ struct Builder {
         auto V = [&]() { return rv(K_SLOT, R.w3 & 0xFFFFu); };
         std::string ax = "W", ay, bx = "W", by;
         bool a_prod = true, b_prod = true, sub_a = false, sub_b = false;
-        std::string body = "const iv W = " + W + "; ";
+        std::string body = "const auto W = " + W + "; ";
         double cost = 0.0;
         switch (op) {
         case OP_ADD: a_prod = b_prod = false; break;
@@ -201,11 +201,11 @@ struct Builder {
             if (!b_none) by = rv(Ak, R.w2 & 0xFFFFu);
             break;
         case OP_DIV:
-            body += "const iv Rb = iv_recip(" + rv(Bk, R.w2 >> 16) + "); ";
+            body += "const auto Rb = iv_recip(" + rv(Bk, R.w2 >> 16) + "); ";
             cost += 4.0;
             ay = "Rb";
             if (!b_none) {
-                body += "const iv nb = iv_neg(iv_mul(W, " + V() + ")); ";   // b gets -(W V) / B
+                body += "const auto nb = iv_neg(iv_mul(W, " + V() + ")); ";   // b gets -(W V) / B
                 bx = "nb";
                 cost += 2.0;
             }
@@ -217,8 +217,8 @@ struct Builder {
         case OP_LOG: if (!a_none) { ay = "iv_recip_pos(" + rv(Ak, R.w2 & 0xFFFFu) + ")"; cost += 4.0; } break;
         default: a_prod = b_prod = false; ax = bx = "entire()";
         }
-        if (!a_none && a_prod) body += "const iv ya = " + ay + "; ";
-        if (!b_none && b_prod) body += "const iv yb = " + by + "; ";
+        if (!a_none && a_prod) body += "const auto ya = " + ay + "; ";
+        if (!b_none && b_prod) body += "const auto yb = " + by + "; ";
         std::string upd;
         if (!a_none) {
             const std::string un = "w" + S(R.w1 & 0xFFFFu), u = un + "$";
@@ -334,7 +334,7 @@ struct Builder {
                 m.code = F + "$ = final_form(1, nie" + S(o) + "$, nie" + S(o) + "$);";
             } else {
                 m.reads.push_back(var("fc" + S(o)));
-                m.code = "{ iv mvf = fc" + S(o) + "$; ";
+                m.code = "{ auto mvf = fc" + S(o) + "$; ";
                 for (int i = 0; i < n; ++i) {
                     m.reads.push_back(var("g" + S(i)));
                     m.reads.push_back(var("X" + S(i)));
@@ -550,6 +550,107 @@ std::string copy_code(const std::string& code, int K, int k) {
     return r;
 }
 
+// Paired form of two subdomains per thread, the dual-pipe arrangement
+// (seg_ilp = 2 with the short operations out of line and an emulation
+// policy): every value is a pair (iv2, d2) of the two subdomains' values, and
+// every interval operation of a statement is one call that computes both
+// copies. The short operations and the long ones (/ sqrt exp log and the
+// reciprocals) are out-of-line functions whose bodies hold the two copies
+// inlined side by side, so the compiler interleaves their independent
+// dependency chains; copy a's endpoint operations run on the FP64 pipe and
+// copy b's short ones under the emulation policy IVB_EMU_B on the integer
+// pipes (bit-identical to the FP64 instructions). Constants stay scalar
+// intervals and convert to pairs of equal copies where they meet a pair.
+// Without an emulation policy the two copies' calls alternate instead (the
+// interleaved form of chunk_fn), which measured faster.
+const char* kPair =
+    "namespace ivb {\n"
+    "struct iv2 {\n"
+    "  iv a, b;\n"
+    "  __device__ __forceinline__ iv2() {}\n"
+    "  __device__ __forceinline__ iv2(const iv& x) : a(x), b(x) {}\n"
+    "  __device__ __forceinline__ iv2(const iv& x, const iv& y) : a(x), b(y) {}\n"
+    "};\n"
+    "struct d2 { double a, b; };\n"
+    "__device__ __forceinline__ iv2 mk(d2 x, d2 y) { return iv2(mk(x.a, y.a), mk(x.b, y.b)); }\n"
+    "__device__ __forceinline__ iv2 ld2(const double* st, int ss, int slot, int ns) {\n"
+    "  return iv2(st_ld(st, ss, slot), st_ld(st, ss, slot + ns)); }\n"
+    "__device__ __forceinline__ d2 ldd2(const double* st, int ss, int slot, int ns) {\n"
+    "  d2 r; r.a = st_d(st, ss, slot); r.b = st_d(st, ss, slot + ns); return r; }\n"
+    "__device__ __forceinline__ void st2(double* st, int ss, int slot, int ns, const iv2& v) {\n"
+    "  st_st(st, ss, slot, v.a); st_st(st, ss, slot + ns, v.b); }\n"
+    "__device__ __forceinline__ void std2(double* st, int ss, int slot, int ns, const d2& v) {\n"
+    "  st_sd(st, ss, slot, v.a); st_sd(st, ss, slot + ns, v.b); }\n"
+    "static __device__ __noinline__ iv2 o_add(iv2 x, iv2 y) {\n"
+    "  return iv2(iv_add_t<0>(x.a, y.a), iv_add_t<IVB_EMU_B>(x.b, y.b)); }\n"
+    "static __device__ __noinline__ iv2 o_sub(iv2 x, iv2 y) {\n"
+    "  return iv2(iv_sub_t<0>(x.a, y.a), iv_sub_t<IVB_EMU_B>(x.b, y.b)); }\n"
+    "static __device__ __noinline__ iv2 o_mul(iv2 x, iv2 y) {\n"
+    "  return iv2(iv_mul_t<0>(x.a, y.a), iv_mul_t<IVB_EMU_B>(x.b, y.b)); }\n"
+    "static __device__ __noinline__ iv2 o_sqr(iv2 x) { return iv2(iv_sqr_t<0>(x.a), iv_sqr_t<IVB_EMU_B>(x.b)); }\n"
+    "static __device__ __noinline__ iv2 o_fma(iv2 x, iv2 y, iv2 z) {\n"
+    "  return iv2(iv_fma(x.a, y.a, z.a), iv_fma(x.b, y.b, z.b)); }\n"
+    "static __device__ __noinline__ iv2 iv_div(iv2 x, iv2 y) { return iv2(iv_div(x.a, y.a), iv_div(x.b, y.b)); }\n"
+    "static __device__ __noinline__ iv2 iv_sqrt(iv2 x) { return iv2(iv_sqrt(x.a), iv_sqrt(x.b)); }\n"
+    "static __device__ __noinline__ iv2 iv_exp(iv2 x) { return iv2(iv_exp(x.a), iv_exp(x.b)); }\n"
+    "static __device__ __noinline__ iv2 iv_log(iv2 x) { return iv2(iv_log(x.a), iv_log(x.b)); }\n"
+    "static __device__ __noinline__ iv2 iv_recip(iv2 x) { return iv2(iv_recip(x.a), iv_recip(x.b)); }\n"
+    "static __device__ __noinline__ iv2 iv_recip_pos(iv2 x) { return iv2(iv_recip_pos(x.a), iv_recip_pos(x.b)); }\n"
+    "__device__ __forceinline__ iv2 iv_neg(iv2 x) { return iv2(iv_neg(x.a), iv_neg(x.b)); }\n"
+    "__device__ __forceinline__ iv2 iv_twice(iv2 x) { return iv2(iv_twice(x.a), iv_twice(x.b)); }\n"
+    "__device__ __forceinline__ iv2 mvf_term(iv2 acc, iv2 g, iv2 x, d2 c) {\n"
+    "  return iv2(mvf_term(acc.a, g.a, x.a, c.a), mvf_term(acc.b, g.b, x.b, c.b)); }\n"
+    "__device__ __forceinline__ iv2 final_form(int f, iv2 m, iv2 v) {\n"
+    "  return iv2(final_form(f, m.a, v.a), final_form(f, m.b, v.b)); }\n"
+    "}\n";
+
+// C++ of one chunk function in the paired form (see kPair)
+std::string chunk_fn_pair(const Builder& B, const Plan& pl, int c, int ns) {
+    const Chunk& ch = pl.chunks[c];
+    const std::map<int, int>& ld = pl.load_slot[c];
+    const std::map<int, int>& stv = pl.store_slot[c];
+    const std::string NS = S(ns);
+    std::string s = "extern \"C\" __device__ __noinline__ void ivb_ck" + S(c) +
+                    "(double* __restrict__ st, const int ss) {\n  using namespace ivb;\n";
+    std::set<int> touched;
+    for (const Stmt& t : ch.body) {
+        for (int v : t.reads) touched.insert(v);
+        for (int v : t.writes) touched.insert(v);
+    }
+    {
+        std::string dv, dd;
+        for (int v : touched) {
+            if (B.vtype[v] == V_DBL) dd += (dd.empty() ? "  d2 " : ", ") + B.vname[v];
+            else dv += (dv.empty() ? "  iv2 " : ", ") + B.vname[v];
+        }
+        if (!dv.empty()) s += dv + ";\n";
+        if (!dd.empty()) s += dd + ";\n";
+    }
+    std::map<int, size_t> last_write;
+    for (size_t i = 0; i < ch.body.size(); ++i)
+        for (int v : ch.body[i].writes) last_write[v] = i;
+    std::set<int> loaded, written;
+    for (size_t i = 0; i < ch.body.size(); ++i) {
+        const Stmt& t = ch.body[i];
+        for (int v : t.reads)
+            if (!written.count(v) && !loaded.count(v)) {
+                s += "  " + B.vname[v] + (B.vtype[v] == V_DBL ? " = ldd2(st, ss, " : " = ld2(st, ss, ") +
+                     S(ld.at(v)) + ", " + NS + ");\n";
+                loaded.insert(v);
+            }
+        s += "  " + copy_code(outline_code(t.code), 1, 0) + "\n";
+        for (int v : t.writes) written.insert(v);
+        for (int v : t.writes) {
+            auto it = stv.find(v);
+            if (last_write[v] == i && it != stv.end())
+                s += std::string(B.vtype[v] == V_DBL ? "  std2(st, ss, " : "  st2(st, ss, ") + S(it->second) + ", " +
+                     NS + ", " + B.vname[v] + ");\n";
+        }
+    }
+    s += "}\n";
+    return s;
+}
+
 // C++ of one chunk function. With K = 2 every statement runs twice, on two
 // subdomains, interleaved: two independent dependency chains per thread.
 // Copy k keeps its values in state slots offset by k * ns.
@@ -621,8 +722,11 @@ const char* kStateHelpers =
     "__device__ __forceinline__ void st_sd(double* st, int ss, int slot, double v) { st[(size_t)(2 * slot) * ss] = v; }\n"
     "}\n";
 
-std::string unit_head(int emulate, bool kernel_unit) {
-    std::string s = "#define IVB_EMU " + S(emulate) + "\n#define IVB_HEAVY static __noinline__\n";
+std::string unit_head(int emulate, bool kernel_unit, bool paired = false) {
+    // paired units: copy a on the FP64 instructions, copy b under the policy;
+    // the long primitives inline into the out-of-line pair functions
+    std::string s = paired ? "#define IVB_EMU 0\n#define IVB_EMU_B " + S(emulate) + "\n#define IVB_HEAVY __forceinline__\n"
+                           : "#define IVB_EMU " + S(emulate) + "\n#define IVB_HEAVY static __noinline__\n";
     if (!kernel_unit) s += "#define IVB_JIT_EXTERN_TABLES\n";
     s += kPrelude;
     s += "#include \"ivb_bound_common.cuh\"\n";
@@ -889,10 +993,13 @@ SegSource jit_seg_source(const HostProgram& P, const std::vector<Ins>& ins, cons
     const int C = (int)pl.chunks.size();
     const int U = std::max(1, std::min(C, pol.units));
     for (int u = 0; u < U; ++u) {
-        std::string src = unit_head(emulate, false);
+        const bool paired = K == 2 && pol.outline && emulate != 0;
+        std::string src = unit_head(emulate, false, paired);
         if (pol.outline) src += kOutline;
+        if (paired) src += kPair;
         const int b = (int)((long long)C * u / U), e = (int)((long long)C * (u + 1) / U);
-        for (int c = b; c < e; ++c) src += chunk_fn(B, pl, c, K, ns, pol.outline);
+        for (int c = b; c < e; ++c)
+            src += paired ? chunk_fn_pair(B, pl, c, ns) : chunk_fn(B, pl, c, K, ns, pol.outline);
         out.units.push_back(src);
     }
     return out;

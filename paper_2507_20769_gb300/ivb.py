@@ -239,7 +239,8 @@ def ivb_specialize_compile(tape, grad_mode="adjoint", compact=True, variant=None
     """generate and compile (NVRTC, no GPU needed) the tape-specialised
     kernel of a tape: ptxas registers, spill-store bytes, compile seconds.
     variant: the `specialize` value it is built as (1 compact, 2 inlined,
-    3 segmented); by default 1 or 2 from `compact`"""
+    3 segmented; 4: segmented with two subdomains per thread in the paired
+    dual-pipe form, emulate = 15); by default 1 or 2 from `compact`"""
     recs = tape.records()
     oi = np.ascontiguousarray(tape.out_idx, dtype=np.int32)
     ok = np.ascontiguousarray(tape.out_kind, dtype=np.uint8)
@@ -247,7 +248,7 @@ def ivb_specialize_compile(tape, grad_mode="adjoint", compact=True, variant=None
                  ok.ctypes.data)
     regs, spill, secs = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
     g = GRAD[grad_mode] if isinstance(grad_mode, str) else int(grad_mode)
-    code = {1: 1, 2: 0, 3: 3}[int(variant)] if variant is not None else int(bool(compact))
+    code = {1: 1, 2: 0, 3: 3, 4: 4}[int(variant)] if variant is not None else int(bool(compact))
     _check(lib().ivb_specialize_compile(ctypes.byref(t), g, code, ctypes.byref(regs),
                                         ctypes.byref(spill), ctypes.byref(secs)))
     return {"registers": regs.value, "spill_bytes": spill.value, "seconds": secs.value}

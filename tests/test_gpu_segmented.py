@@ -303,6 +303,38 @@ def test_two_subdomains_per_thread_identical_to_interpreter(form, sync):
         assert same_bits(a[k], b[k]), k
 
 
+@pytest.mark.parametrize("emulate", [3, 12, 15])
+def test_paired_form_with_emulated_second_copy_bit_exact(emulate):
+    """two subdomains per thread in the paired form, the second copy's
+    products and sums on the integer-pipe emulation: the oracle's bits on a
+    rational tape, the interpreter's on configuration 2 (exp/log)"""
+    t = rational_problem(n=3, K=50, n_ineq=3)
+    boxes, splits = ragged_batch(t, 31, seed=23)
+    with ivb.Problem(t, specialize=3, seg_ilp=2, emulate=emulate, seg_chunk=24) as p:
+        assert p.get_segmentation()["ilp"] == 2
+        r = p.bound_nodes_ex(boxes, splits, want_hull=True)
+    ref = oracle.bound_nodes(t, boxes, splits, grad_mode="adjoint", tight=True)
+    for k in ("lb", "ub", "minlo", "maxhi"):
+        assert np.array_equal(r[k], ref[k]), k
+    assert np.array_equal(r["infeasible"].astype(bool), ref["infeasible"])
+    t2 = W.config_tape(2)
+    boxes, splits = ragged_batch(t2, 19, seed=8)
+    a, b = bound_seg_and_interp(t2, boxes, splits, dict(seg_ilp=2, emulate=emulate))
+    for k in KEYS:
+        assert same_bits(a[k], b[k]), k
+
+
+def test_two_subdomains_inlined_interleaved_bit_exact():
+    """seg_ilp = 2 with the short operations inlined (every statement written
+    twice, interleaved, instead of the paired calls): the interpreter's bits
+    on configuration 2"""
+    t2 = W.config_tape(2)
+    boxes, splits = ragged_batch(t2, 21, seed=9)
+    a, b = bound_seg_and_interp(t2, boxes, splits, dict(seg_ilp=2, seg_outline=0))
+    for k in KEYS:
+        assert same_bits(a[k], b[k]), k
+
+
 @pytest.mark.parametrize("recompute", [0, 1])
 @pytest.mark.parametrize("tpsub", [1, 2])
 def test_inlined_short_operations_bit_exact(recompute, tpsub):

@@ -52,14 +52,16 @@ def test_specialize_compile_rejects_invalid_tape(ivb):
     assert e.value.status == ivb.IVB_ETAPE
 
 
+@pytest.mark.parametrize("variant", [3, 4])
 @pytest.mark.parametrize("which", ["every_op", "config2"])
-def test_segmented_kernel_compiles(ivb, which):
-    """the segmented kernel (specialize = 3): chunk functions compiled in
+def test_segmented_kernel_compiles(ivb, which, variant):
+    """the segmented kernel (specialize = 3; variant 4: two subdomains per
+    thread in the paired dual-pipe form): chunk functions compiled in
     parallel as relocatable programs and linked, within the register budget"""
     t = every_op_tape() if which == "every_op" else W.config_tape(2)
-    r = ivb.ivb_specialize_compile(t, "adjoint", variant=3)
+    r = ivb.ivb_specialize_compile(t, "adjoint", variant=variant)
     assert 0 < r["registers"] <= 128
     assert r["spill_bytes"] >= 0 and r["seconds"] > 0
     with pytest.raises(ivb.IvbError) as e:
-        ivb.ivb_specialize_compile(t, "forward", variant=3)
+        ivb.ivb_specialize_compile(t, "forward", variant=variant)
     assert e.value.status == ivb.IVB_EINVAL
