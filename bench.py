@@ -415,9 +415,9 @@ def kernel_desc(p, create_s=None):
 
 def kernel_compare(t, boxes_d, splits_d, out, flush, stream, subs_step, step_s, dev):
     """the same step through each kernel on its own (bit-identical bounds):
-    the tape interpreter, and the segmented tape-specialised kernel with its
-    reverse-segment recomputation (policy 1) -- the two the library's
-    autotuner chooses between for these tapes"""
+    the tape interpreter, and the segmented tape-specialised kernel with the
+    library's segmentation defaults -- the two the library's autotuner
+    chooses between for these tapes"""
     import torch
     from paper_2507_20769_gb300 import ivb
     res = {}
@@ -485,7 +485,7 @@ def config2_step(dev, flush, stream, steps=5):
 KERNEL_SOURCES = {
     "interpreter": ("ivb_kernels.cu", "ivb_bound_common.cuh", "ivb_iv.cuh", "ivb_fp64x.cuh", "ivb_emu.cuh"),
     "specialised": ("ivb_jit.cpp", "ivb_bound_common.cuh", "ivb_iv.cuh", "ivb_fp64x.cuh", "ivb_emu.cuh"),
-    "segmented": ("ivb_jit_seg.cpp", "ivb_bound_common.cuh", "ivb_iv.cuh", "ivb_fp64x.cuh", "ivb_emu.cuh"),
+    "segmented": ("ivb_jit_seg.cpp", "ivb_jit.h", "ivb_bound_common.cuh", "ivb_iv.cuh", "ivb_fp64x.cuh", "ivb_emu.cuh"),
 }
 
 

@@ -146,7 +146,10 @@ typedef struct {
                                   instead of read back from the state area:
                                   0 none, 1 the cheap operations (+ - * sqr
                                   neg; the values of / sqrt exp log are
-                                  stored), 2 all; -1 (default): 1           */
+                                  stored), 2 all; -1 (default): the
+                                  library's choice, now 0 (on this part the
+                                  recomputed FP64 work costs more than the
+                                  state traffic it saves)                  */
     int32_t seg_chunk;         /* segmented kernel: estimated FP64 issue
                                   slots per chunk (0 = default 320)         */
     int32_t seg_regs;          /* segmented kernel: register budget of every

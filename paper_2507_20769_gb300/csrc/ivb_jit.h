@@ -61,7 +61,7 @@ struct JitKernel {
 struct SegPolicy {
     double chunk_cost = 320.0;   // estimated FP64 issue slots per chunk
     int chunk_stmts = 96;        // statements per chunk
-    int recompute = 1;
+    int recompute = 0;           // measured fastest: recomputation adds FP64 work, the state area streams with room to spare
     int units = 16;
     int max_regs = 128;          // register budget of every chunk function
     int ilp = 1;                 // subdomains per thread (1, or 2 interleaved)
