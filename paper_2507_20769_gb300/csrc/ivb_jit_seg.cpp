@@ -16,13 +16,15 @@
 //    in global memory (element u of thread t at state[u * blockDim + t],
 //    coalesced across a warp), stored right after the statement that writes
 //    it and loaded where the next chunk first reads it;
-//  * a reverse chunk does not read the forward values of its own segment from
-//    memory: it recomputes them from the segment's checkpoints (the values
-//    that enter the segment from earlier statements) before running its
-//    reverse statements -- tape recomputation instead of storing the whole
-//    forward sweep. Policy 1 recomputes the cheap operations (+ - * sqr neg)
-//    and keeps the values of the long ones (/ sqrt exp log) in the state area;
-//    policy 2 recomputes every operation of the segment; policy 0 stores every
+//  * with a recomputation policy a reverse chunk does not read the forward
+//    values of its own segment from memory: it recomputes them from the
+//    segment's checkpoints (the values that enter the segment from earlier
+//    statements) before running its reverse statements -- tape recomputation
+//    instead of storing the whole forward sweep. Policy 1 recomputes the cheap
+//    operations (+ - * sqr neg) and keeps the values of the long ones
+//    (/ sqrt exp log) in the state area; policy 2 recomputes every operation
+//    of the segment; policy 0 (the default: on a narrow FP64 pipe the
+//    recomputed work costs more than the state traffic it saves) stores every
 //    forward value the reverse sweep reads.
 // Every statement calls the same interval primitive on the same operands as
 // the interpreter, a recomputed value is the same function of the same
