@@ -179,8 +179,10 @@ typedef struct {
     int32_t seg_outline;       /* segmented kernel: 1 calls + - * sqr and the
                                   fused accumulation out of line (a third of
                                   the code every warp streams through, a call
-                                  per statement); 0 inlines them; -1
-                                  (default): the library's choice, now 1    */
+                                  per statement); 2 only * sqr and the fused
+                                  accumulation (+ and - inline); 0 inlines
+                                  them all; -1 (default): the library's
+                                  choice, now 1                             */
 } ivb_options;
 
 typedef struct ivb_problem ivb_problem;

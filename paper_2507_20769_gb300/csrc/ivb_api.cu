@@ -420,7 +420,7 @@ SegPolicy seg_policy(const ivb_options& o) {
     if (o.recompute >= 0) pol.recompute = o.recompute;
     if (o.seg_chunk > 0) pol.chunk_cost = o.seg_chunk;
     if (o.seg_ilp > 0) pol.ilp = o.seg_ilp;
-    pol.outline = o.seg_outline != 0;   // -1: the library's choice, out of line
+    pol.outline = o.seg_outline < 0 ? 1 : o.seg_outline;   // -1: the library's choice, all out of line
     if (o.seg_regs > 0) pol.max_regs = o.seg_regs;
     const unsigned hc = std::thread::hardware_concurrency();
     pol.units = std::max(1, std::min(64, hc ? (int)hc : 8));
@@ -537,7 +537,7 @@ extern "C" ivb_status ivb_create_problem(const ivb_tape* tape, const ivb_options
         return fail(nullptr, IVB_EINVAL, "threads_per_subdomain must be 0 (tuned), 1, 2 or 4");
     if (o.seg_sync < -1 || o.seg_sync > 1) return fail(nullptr, IVB_EINVAL, "seg_sync must be -1, 0 or 1");
     if (o.seg_ilp < 0 || o.seg_ilp > 2) return fail(nullptr, IVB_EINVAL, "seg_ilp must be 0, 1 or 2");
-    if (o.seg_outline < -1 || o.seg_outline > 1) return fail(nullptr, IVB_EINVAL, "seg_outline must be -1, 0 or 1");
+    if (o.seg_outline < -1 || o.seg_outline > 2) return fail(nullptr, IVB_EINVAL, "seg_outline must be -1, 0, 1 or 2");
     if (o.seg_regs != 0 && (o.seg_regs < 64 || o.seg_regs > 255))
         return fail(nullptr, IVB_EINVAL, "seg_regs must be 0 or in [64, 255]");
     if (o.emulate < -1 || o.emulate > 15) return fail(nullptr, IVB_EINVAL, "emulate must be -1 or a bitmask in [0, 15]");

@@ -65,7 +65,7 @@ struct SegPolicy {
     int units = 16;
     int max_regs = 128;          // register budget of every chunk function
     int ilp = 1;                 // subdomains per thread (1, or 2 interleaved)
-    bool outline = true;         // short interval operations called out of line
+    int outline = 1;             // short interval operations out of line: 0 none, 1 all, 2 products only
 };
 struct SegSource {
     std::string kernel;               // tile loop, Step 1, chunk calls, Step 3 (one kernel per T)

@@ -526,10 +526,14 @@ const char* kOutline =
     "static __device__ __noinline__ iv o_fma(iv a, iv b, iv c) { return iv_fma(a, b, c); }\n"
     "}\n";
 
-// the statement's code with the short operations called out of line
-std::string outline_code(const std::string& code) {
+// the statement's code with the short operations called out of line: all of
+// them (level 1) or the products only (level 2: x sqr and the fused
+// accumulation; + and - stay inline)
+std::string outline_code(const std::string& code, int level = 1) {
     std::string r = code;
     for (const char* f : {"iv_add(", "iv_sub(", "iv_mul(", "iv_sqr(", "iv_fma("}) {
+        const bool sum = f[3] == 'a' || (f[3] == 's' && f[4] == 'u');   // iv_add, iv_sub
+        if (level == 2 && sum) continue;
         const std::string from = f, to = std::string("o_") + (f + 3);
         size_t at = 0;
         while ((at = r.find(from, at)) != std::string::npos) {
@@ -656,7 +660,7 @@ std::string chunk_fn_pair(const Builder& B, const Plan& pl, int c, int ns) {
 // C++ of one chunk function. With K = 2 every statement runs twice, on two
 // subdomains, interleaved: two independent dependency chains per thread.
 // Copy k keeps its values in state slots offset by k * ns.
-std::string chunk_fn(const Builder& B, const Plan& pl, int c, int K, int ns, bool outline) {
+std::string chunk_fn(const Builder& B, const Plan& pl, int c, int K, int ns, int outline) {
     const Chunk& ch = pl.chunks[c];
     const std::map<int, int>& ld = pl.load_slot[c];
     const std::map<int, int>& stv = pl.store_slot[c];
@@ -694,7 +698,7 @@ std::string chunk_fn(const Builder& B, const Plan& pl, int c, int K, int ns, boo
                 }
                 loaded.insert(v);
             }
-        for (int k = 0; k < K; ++k) s += "  " + copy_code(outline ? outline_code(t.code) : t.code, K, k) + "\n";
+        for (int k = 0; k < K; ++k) s += "  " + copy_code(outline ? outline_code(t.code, outline) : t.code, K, k) + "\n";
         for (int v : t.writes) written.insert(v);
         for (int v : t.writes) {
             auto it = stv.find(v);

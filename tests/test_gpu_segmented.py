@@ -136,7 +136,7 @@ def test_segmented_feasibility_filter_and_ub_match_oracle(kind, filt):
 def test_segmented_rejects_forward_mode_and_bad_options():
     t = rational_problem()
     for bad in (dict(specialize=3, grad_mode="forward"), dict(specialize=3, recompute=3),
-                dict(specialize=3, seg_regs=32), dict(specialize=4)):
+                dict(specialize=3, seg_regs=32), dict(specialize=4), dict(specialize=3, seg_outline=3)):
         with pytest.raises(ivb.IvbError) as e:
             ivb.Problem(t, **bad)
         assert e.value.status == ivb.IVB_EINVAL
@@ -320,6 +320,24 @@ def test_paired_form_with_emulated_second_copy_bit_exact(emulate):
     t2 = W.config_tape(2)
     boxes, splits = ragged_batch(t2, 19, seed=8)
     a, b = bound_seg_and_interp(t2, boxes, splits, dict(seg_ilp=2, emulate=emulate))
+    for k in KEYS:
+        assert same_bits(a[k], b[k]), k
+
+
+def test_products_only_out_of_line_bit_exact():
+    """seg_outline = 2 (x, sqr and the fused accumulation called out of line,
+    + and - inline): the oracle's bits on a rational tape, the interpreter's
+    on configuration 2"""
+    t = rational_problem(n=3, K=50, n_ineq=3)
+    boxes, splits = ragged_batch(t, 27, seed=29)
+    with ivb.Problem(t, specialize=3, seg_outline=2, seg_chunk=24) as p:
+        r = p.bound_nodes_ex(boxes, splits, want_hull=True)
+    ref = oracle.bound_nodes(t, boxes, splits, grad_mode="adjoint", tight=True)
+    for k in ("lb", "ub", "minlo", "maxhi"):
+        assert np.array_equal(r[k], ref[k]), k
+    t2 = W.config_tape(2)
+    boxes, splits = ragged_batch(t2, 15, seed=10)
+    a, b = bound_seg_and_interp(t2, boxes, splits, dict(seg_outline=2))
     for k in KEYS:
         assert same_bits(a[k], b[k]), k
 
