@@ -24,3 +24,44 @@ def test_reference_arm_prints_contract_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in line["config"]
+
+
+def _load_bench():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_traffic_record_scales_by_subdomains_and_expires_with_the_sources(tmp_path, monkeypatch):
+    """roofline.traffic: the committed ncu bytes per subdomain scaled to the
+    launch, reported only while the kernel's sources hash to the profiled
+    ones (a changed kernel reports null until it is profiled again)"""
+    b = _load_bench()
+    (tmp_path / "profiles").mkdir()
+    rec = {"segmented": {"dram_bytes_per_subdomain": 1000.5, "kernel_sha256": "abc"}}
+    (tmp_path / "profiles" / "bound_traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(b, "ROOT", str(tmp_path))
+    monkeypatch.setattr(b, "kernel_sha", lambda which: "abc")
+    assert b.traffic_for(1 << 24, "segmented") == 1000.5 * (1 << 24)
+    assert b.traffic_for(4, "segmented") == 4002.0
+    assert b.traffic_for(1 << 24, "interpreter") is None
+    monkeypatch.setattr(b, "kernel_sha", lambda which: "abd")
+    assert b.traffic_for(1 << 24, "segmented") is None
+
+
+def test_committed_traffic_records_name_existing_sources():
+    """every committed record lists the sources its hash covers, and those
+    are the files bench.py hashes for that kernel"""
+    b = _load_bench()
+    with open(os.path.join(ROOT, "profiles", "bound_traffic.json")) as fh:
+        recs = json.load(fh)
+    for which, rec in recs.items():
+        assert which in b.KERNEL_SOURCES, which
+        assert tuple(rec["sources"]) == tuple(b.KERNEL_SOURCES[which]), which
+        for name in rec["sources"]:
+            assert os.path.exists(os.path.join(ROOT, "paper_2507_20769_gb300", "csrc", name)), name
+        assert rec["dram_bytes_per_subdomain"] > 0 and rec["subdomains"] > 0
+        per = (rec["dram_bytes_read"] + rec["dram_bytes_write"]) / rec["subdomains"]
+        assert abs(per - rec["dram_bytes_per_subdomain"]) <= 1e-9 * per
