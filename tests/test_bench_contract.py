@@ -65,3 +65,36 @@ def test_committed_traffic_records_name_existing_sources():
         assert rec["dram_bytes_per_subdomain"] > 0 and rec["subdomains"] > 0
         per = (rec["dram_bytes_read"] + rec["dram_bytes_write"]) / rec["subdomains"]
         assert abs(per - rec["dram_bytes_per_subdomain"]) <= 1e-9 * per
+
+
+def test_roofline_fraction_is_algorithmic_endpoint_operations_over_the_fp64_peak(monkeypatch):
+    """roofline.frac = endpoint operations per subdomain (the static counts) x
+    subdomains of a step / step time / (2 FP64 lanes per clock per SM x SMs x
+    the sampled SM clock); independent of how fast the primitives run"""
+    import types
+    import torch
+    b = _load_bench()
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda dev: types.SimpleNamespace(multi_processor_count=152))
+    monkeypatch.setattr(b, "traffic_for", lambda subs, which: None)
+    counts = {"addsub": 14188, "mul": 31542, "div": 1844, "rcp": 2730, "sqrt": 1892, "exp": 1872, "log": 1724, "rn": 48}
+
+    class FakeProblem:
+        def op_counts(self):
+            return dict(counts)
+
+        def get_segmentation(self):
+            return {"recomputed": 0}
+
+        def get_tuning(self):
+            return {"kernel": 2}
+
+    subs, step_s = 1 << 24, 3.7
+    rf = b.roofline_block(FakeProblem(), subs, step_s, {"sm_mhz": 2070.0}, 0)
+    peak = 2.0 * 152 * 2070e6
+    assert rf["bound"] == "alu" and rf["kernel"] == "segmented"
+    assert rf["work_per_subdomain"]["endpoint_ops"] == 55840
+    assert abs(rf["frac"] - 55840 * subs / step_s / peak) <= 1e-12
+    assert abs(rf["achieved"] - 55840 * subs / step_s / 1e9) <= 1e-9 * rf["achieved"]
+    assert abs(rf["peak"] - peak / 1e9) <= 1e-9
+    rf2 = b.roofline_block(FakeProblem(), subs, step_s, {"sm_mhz": None}, 0)   # no clock sample: maximum clock
+    assert abs(rf2["peak"] - peak / 1e9) <= 1e-9
